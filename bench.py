@@ -1,0 +1,364 @@
+"""Benchmark: A+A' pairs/s (one MLEM iteration = one A and one A' pass plus the
+fused update) on the paper-scale workload 128x128x80, 128 views, 37x37
+depth-dependent anisotropic Gaussian PSF (separable factors), FP32.
+
+One step = one EM iteration x <- x A'(y/(Ax + rbar)) / A'1 over the whole
+synthetic problem.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per GPU, launched by torchrun); the
+path has no exchange step, so no collective is used on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "A+A' pairs/s at 128x128x80, 128 views"
+UNIT = "pairs/s"
+NX, NZ, NVIEW, PSF = 128, 80, 128, 37
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--path", choices=["separable", "direct"], default="separable")
+    ap.add_argument("--direct-steps", type=int, default=3, help="steps of the full-PSF path reported beside (0: skip)")
+    ap.add_argument("--cpu-views", type=int, default=0, help="views in the CPU baseline sample (0: auto)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks sampler
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- workload
+def make_workload(device, path):
+    import torch
+
+    from paper_2301_09710_gb300 import SpectPlan, synthetic
+
+    prob = synthetic.config2(seed=0, nx=NX, nz=NZ, nview=NVIEW, psf_size=PSF)
+    sep = path == "separable"
+    if sep:
+        plan = SpectPlan(NX, NZ, NVIEW, mu=prob.mu, dy=prob.dy, fx=prob.fx, fz=prob.fz, device=device)
+    else:
+        plan = SpectPlan(NX, NZ, NVIEW, mu=prob.mu, dy=prob.dy, psf=prob.full_psf(), device=device)
+    xt = torch.from_numpy(prob.x).to(device)
+    primary = plan.forward(xt)
+    scale = 1e7 / float(primary.sum())
+    primary = (primary * scale).cpu().numpy()
+    rbar = synthetic.background_from(primary, 0.1, 8.0)
+    y = synthetic.poisson_counts(primary + rbar, 0)
+    x0 = np.where(prob.body, 1.0, 0.0).astype(np.float32)
+    return prob, plan, x0, y, rbar
+
+
+def algorithmic_flops(kind: str, nv: int, sep: bool) -> float:
+    """Algorithmic FLOPs of one launch of a kernel class that processes nv views."""
+    vv = float(NX) * NX * NZ * nv  # voxel-views
+    conv = 2.0 * (PSF + PSF) if sep else 2.0 * PSF * PSF
+    return {"conv_fwd": conv * vv, "conv_adj": conv * vv, "rotate_atten": 20.0 * vv, "rotate_adj": 8.0 * vv}.get(kind, 0.0)
+
+
+def peaks(torch, dev_index):
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    mp = json.load(open(path)) if os.path.exists(path) else {}
+    props = torch.cuda.get_device_properties(dev_index)
+    sms = props.multi_processor_count
+    clk = float(mp.get("sm_max_mhz", 2070.0))
+    fp32 = sms * 128 * 2 * clk * 1e6 / 1e12  # TFLOP/s: 128 FP32 lanes/SM, FMA = 2 FLOP
+    return {"sms": sms, "sm_max_mhz": clk, "fp32_tflops": fp32, "hbm_gbs": mp.get("hbm_gbs")}
+
+
+def run_ours(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+    from __graft_entry__ import build
+    build()
+
+    prob, plan, x0_h, y_h, rbar_h = make_workload(device, args.path)
+    sep = plan.info()["separable"]
+    y = torch.from_numpy(y_h).to(device)
+    rbar = torch.from_numpy(rbar_h).to(device)
+    x = torch.from_numpy(x0_h).to(device)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    stream = torch.cuda.current_stream()
+
+    plan.em_step(x, y, rbar, niter=1)  # caches A'1
+    for _ in range(args.warmup):
+        plan.em_step(x, y, rbar, niter=1)
+    torch.cuda.synchronize()
+
+    def timed_steps(k):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for a, b in ev:
+            flush.fill_(1.0)  # evict L2 between steps (outside the timed events)
+            a.record(stream)
+            plan.em_step(x, y, rbar, niter=1)
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev)
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    plan.profile_read(reset=True)
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        total_ms = timed_steps(args.steps)
+        wall = time.perf_counter() - t0
+    launches = plan.profile_read(reset=True)
+    if dist:
+        t = torch.tensor([total_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+    n_launch = sum(v[0] for v in launches.values())
+
+    # per-kernel device time on the launch stream (second pass, events around every launch)
+    plan.profile(True)
+    timed_steps(args.steps)
+    prof = plan.profile_read(reset=True)
+    plan.profile(False)
+    pk = peaks(torch, local)
+    chunk = plan.info()["view_chunk"]
+    kern = {}
+    for k, (n, ms) in prof.items():
+        if n == 0:
+            continue
+        nv_avg = NVIEW * args.steps / n if k != "other" else 0
+        fl = algorithmic_flops(k, nv_avg, sep) if k != "other" else 0.0
+        kern[k] = {"launches": n, "ms_total": ms, "ms_avg": ms / n, "share": None,
+                   "tflops": (fl / (ms / n * 1e-3) / 1e12) if ms > 0 and fl else None}
+    tot = sum(v["ms_total"] for v in kern.values())
+    for v in kern.values():
+        v["share"] = v["ms_total"] / tot if tot else None
+    dom = max(kern, key=lambda k: kern[k]["ms_total"])
+    achieved = kern[dom]["tflops"]
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
+                "frac": (achieved / pk["fp32_tflops"]) if achieved else None, "traffic": None,
+                "peak_basis": f"{pk['sms']} SMs x 128 FP32 lanes x 2 FLOP x {pk['sm_max_mhz']:.0f} MHz (max SM clock)",
+                "kernels": kern}
+
+    # end to end through the public API: host (pinned) buffers, copies inside the timed region
+    xh = torch.from_numpy(x0_h).pin_memory()
+    yh = torch.from_numpy(y_h).pin_memory()
+    rh = torch.from_numpy(rbar_h).pin_memory()
+    xo = torch.empty_like(xh).pin_memory()
+    xd, yd, rd = torch.empty_like(x), torch.empty_like(y), torch.empty_like(rbar)
+    torch.cuda.synchronize()
+    e_ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        xd.copy_(xh, non_blocking=True)
+        yd.copy_(yh, non_blocking=True)
+        rd.copy_(rh, non_blocking=True)
+        plan.em_step(xd, yd, rd, niter=1)
+        xo.copy_(xd, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e_ms += a.elapsed_time(b)
+    e2e = {"value": world * args.steps / (e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(xh.numel() * 4 + yh.numel() * 4 + rh.numel() * 4),
+           "d2h_bytes_per_step": int(xo.numel() * 4)}
+
+    direct = None
+    if args.direct_steps > 0 and args.path == "separable":
+        plan.close()
+        _, dplan, _, _, _ = make_workload(device, "direct")
+        xd2 = torch.from_numpy(x0_h).to(device)
+        dplan.em_step(xd2, y, rbar, niter=1)
+        torch.cuda.synchronize()
+        dl = []
+        for _ in range(args.direct_steps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dplan.em_step(xd2, y, rbar, niter=1)
+            b.record(stream)
+            b.synchronize()
+            dl.append(a.elapsed_time(b))
+        dms = sum(dl) / len(dl)
+        direct = {"value": 1e3 / dms, "unit": UNIT, "ms_per_step": dms,
+                  "gflop_per_pair": 2 * algorithmic_flops("conv_fwd", NVIEW, False) / 1e9,
+                  "note": "same workload with the full 37x37 PSF stack (direct 2D blur, no separability)"}
+        dplan.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, prob, x0_h, y_h, rbar_h)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": "128x128x80 image, 128 views over 360 deg, 37x37 depth-dependent "
+                                      "anisotropic Gaussian PSF (separable factors), MLEM step with 10% smoothed "
+                                      "background, XCAT-like ellipsoid phantom (seed 0)",
+                          "path": args.path, "view_chunk": chunk, "parallelism": f"replicas{world}",
+                          "l2": "flushed between timed steps (256 MB write)",
+                          "step": "one EM iteration = one A + one A' + fused ratio/update"},
+               "clocks": clk.summary(), "gpu_launches": n_launch, "e2e": e2e, "roofline": roofline,
+               "cpu_baseline": cpu, "wall_s_timed_region": wall}
+        if direct:
+            out["direct_path"] = direct
+        print(json.dumps(out))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(args, prob, x0, y, rbar, budget_views=None):
+    """The FP64 oracle on the host cores, one EM step over a view sample, scaled to pairs/s."""
+    import oracle
+    nth = oracle.max_threads()
+    nsub = args.cpu_views or budget_views or max(4, min(16, nth))
+    views = np.linspace(0, NVIEW, nsub, endpoint=False).astype(int)
+    ang = oracle.default_angles(NVIEW)[views]
+    psf = oracle.psf_from_factors(prob.fx, prob.fz)
+    s = oracle.sensitivity(prob.mu, psf, prob.dy, ang, nthreads=nth)  # cached per plan, not timed
+    t0 = time.perf_counter()
+    oracle.em_step(x0, y[views], rbar[views], prob.mu, psf, prob.dy, ang, s=s, nthreads=nth)
+    dt = time.perf_counter() - t0
+    return {"value": (nsub / NVIEW) / dt, "unit": UNIT, "cores": nth, "kind": "oracle",
+            "sample": f"one FP64 EM step (A + A' over {nsub} of 128 views, full 128x128x80 volume, 37x37 PSF); "
+                      f"{dt:.1f} s, scaled by {nsub}/128", "cpu": cpu_name()}
+
+
+def cpu_name():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return os.uname().machine
+
+
+def run_reference(args):
+    """The oracle as it stands on the host cores, each step a bounded view sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2301_09710_gb300 import synthetic
+    oracle.build()
+    prob = synthetic.config2(seed=0, nx=NX, nz=NZ, nview=NVIEW, psf_size=PSF)
+    nth = oracle.max_threads()
+    nsub = args.cpu_views or max(2, min(8, nth // 2))
+    views = np.linspace(0, NVIEW, nsub, endpoint=False).astype(int)
+    ang = oracle.default_angles(NVIEW)[views]
+    psf = oracle.psf_from_factors(prob.fx, prob.fz)
+    s = oracle.sensitivity(prob.mu, psf, prob.dy, ang, nthreads=nth)
+    x = np.where(prob.body, 1.0, 0.0)
+    v = oracle.forward(prob.x, prob.mu, psf, prob.dy, ang, nthreads=nth)
+    y = synthetic.poisson_counts(v * (1e7 / v.sum() * nsub / NVIEW), 0)
+    rbar = synthetic.background_from(v.astype(np.float32), 0.1, 8.0)
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        x = oracle.em_step(x, y, rbar, prob.mu, psf, prob.dy, ang, s=s, nthreads=nth)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        x = oracle.em_step(x, y, rbar, prob.mu, psf, prob.dy, ang, s=s, nthreads=nth)
+    dt = time.perf_counter() - t0
+    value = args.steps * (nsub / NVIEW) / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3 * NVIEW / nsub, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "128x128x80 image, 128 views, 37x37 PSF, MLEM step (oracle on a view sample)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": nth,
+                         "sample": f"each step: one FP64 EM step over {nsub} of 128 views, scaled by {nsub}/128",
+                         "cpu": cpu_name()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

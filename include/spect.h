@@ -1,0 +1,208 @@
+/*
+ * spect.h -- C ABI of the GB300 (sm_103a) SPECT projector library.
+ *
+ * The operator is the rotation-based SPECT system model of Li, Dewaraja &
+ * Fessler, "Training end-to-end unrolled iterative neural networks for SPECT
+ * image reconstruction" (arXiv 2301.09710), Section II-A:
+ *
+ *   A  (Algorithm 1): for every view l, rotate the image x and the
+ *      attenuation map mu about the axial (z) axis by theta_l with bilinear
+ *      interpolation and zero padding; weight the rotated image by the
+ *      accumulated attenuation of Eq. (1); blur every depth plane j with
+ *      that depth's PSF p(:,:,j,l) (convolution, replicate padding in i and
+ *      k); sum over depth.
+ *   A' (Algorithm 2): the exact transpose of A, satisfying Eq. (2)
+ *      <A x, y> = <x, A' y> up to FP32 rounding.
+ *   EM (Eqs. (7)-(8) with beta = 0): x <- x * A'(y / (A x + rbar)) / A'1.
+ *
+ * All arithmetic is FP32 on the GPU.  Every entry point takes device
+ * pointers unless stated otherwise; no entry point allocates on the caller's
+ * behalf except spect_plan_create (the plan's own state).
+ *
+ * ---------------------------------------------------------------- layouts
+ * 0-based indices (the paper's are 1-based).  All arrays are dense FP32 with
+ * the first index fastest:
+ *   image  x, mu : nx*ny*nz,            x(i,j,k)   at i + nx*(j + ny*k)
+ *   projections v: nx*nz*nview,         v(i,k,l)   at i + nx*(k + nz*l)
+ *   full PSF     : px*pz*ny*nview_psf,  p(a,b,j,l) at a + px*(b + pz*(j + ny*l))
+ *   PSF factors  : fx px*ny*nview_psf at a + px*(j + ny*l),
+ *                  fz pz*ny*nview_psf at b + pz*(j + ny*l),
+ *                  meaning p(a,b,j,l) = fx(a,j,l) * fz(b,j,l).
+ * Plane j = ny-1 of the rotated image is the one nearest the detector
+ * (Eq. (1)); the PSF depth index j refers to that rotated frame.
+ *
+ * ---------------------------------------------------------------- geometry
+ * Rotation centre c = (nx-1)/2.  Output pixel (i,j) of the rotated slice
+ * samples the input at xs = c + cos(t)(i-c) + sin(t)(j-c),
+ * ys = c - sin(t)(i-c) + cos(t)(j-c) (the content turns by +t); cosine and
+ * sine are exact at multiples of pi/2.  The PSF centre is ((px-1)/2,
+ * (pz-1)/2); px and pz must be odd.  Default angles (angles == NULL) are
+ * theta_l = 2*pi*l/nview, the paper's 2*pi*(l-1)/nview with 1-based l.
+ *
+ * ---------------------------------------------------------------- errors
+ * Every entry point returns a spect_status.  Argument errors (SPECT_EINVAL)
+ * are detected on the host before any work is queued and leave no side
+ * effect.  Work is queued on the given stream and is asynchronous; launch
+ * failures are reported as SPECT_ECUDA.  spect_last_error() returns a
+ * thread-local, human-readable message for the last non-OK status.
+ * A plan is not safe for concurrent use from several streams or threads:
+ * calls on one plan must be ordered (same stream, or synchronised).
+ * Input and output buffers of one call must not overlap.
+ */
+#ifndef SPECT_H
+#define SPECT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* spect_stream;
+
+typedef struct spect_plan_s* spect_plan;
+
+typedef enum {
+    SPECT_OK = 0,
+    SPECT_EINVAL = 1,       /* bad argument: size, pointer, alignment, flag  */
+    SPECT_ENOMEM = 2,       /* device allocation for the plan failed         */
+    SPECT_ECUDA = 3,        /* a CUDA call or kernel launch failed           */
+    SPECT_ETIMEOUT = 4,     /* reserved: a bounded device wait gave up       */
+    SPECT_EUNSUPPORTED = 5  /* valid request this build cannot serve         */
+} spect_status;
+
+/* Plan flags. */
+enum {
+    SPECT_PLAN_DEFAULT = 0u,
+    /* Use the separable factors when both a full PSF and factors are given
+     * (otherwise the full PSF wins).  Ignored when only one form is given. */
+    SPECT_PLAN_PREFER_SEPARABLE = 1u << 0
+};
+
+/*
+ * spect_plan_create -- build the operator A for one geometry (Algorithm 1
+ * inputs: attenuation map, 4D PSF, voxel size; Section II-A).
+ *
+ *   out        receives the plan handle (host pointer, must not be NULL).
+ *   nx,ny,nz   image size; nx == ny is required (rotation in the x-y plane);
+ *              2 <= nx <= 1024, 1 <= nz <= 4096.
+ *   nview      number of views, 1..4096.
+ *   mu         device, nx*ny*nz FP32 attenuation coefficients (per unit of
+ *              dy), non-negative; may be NULL for no attenuation.
+ *   dy         voxel size along the depth direction (Eq. (1) Delta_y), >= 0.
+ *   psf        device, full PSF stack (layout above), or NULL.
+ *   psf_fx,
+ *   psf_fz     device, separable factors (layout above), or both NULL.
+ *              At least one of psf / (psf_fx, psf_fz) must be given.
+ *   px, pz     PSF size, odd, 1..127.
+ *   nview_psf  nview (view-dependent PSF, non-circular orbits) or 1
+ *              (the same PSF stack for every view).
+ *   angles     HOST, nview angles in radians, or NULL for the defaults.
+ *   flags      SPECT_PLAN_* bits.
+ *   stream     stream used for the plan's set-up work.
+ *
+ * The plan copies mu and the PSF into its own device memory and builds its
+ * rotation adjacency tables; the call synchronises `stream` before it
+ * returns, so the caller may free or reuse its inputs afterwards.
+ * Errors: SPECT_EINVAL (sizes, NULL out, misaligned or missing inputs),
+ * SPECT_ENOMEM, SPECT_ECUDA.  On error *out is set to NULL.
+ */
+spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nview,
+                               const float* mu, float dy,
+                               const float* psf, const float* psf_fx, const float* psf_fz,
+                               int px, int pz, int nview_psf,
+                               const double* angles, unsigned flags, spect_stream stream);
+
+/*
+ * spect_forward -- v = A x (Algorithm 1).
+ *   x  device, nx*ny*nz (image layout), read only.
+ *   v  device, nx*nz*nview (projection layout), overwritten.
+ * Both 16-byte aligned.  Errors: SPECT_EINVAL (NULL plan/pointer,
+ * misalignment), SPECT_ECUDA.
+ */
+spect_status spect_forward(spect_plan plan, const float* x, float* v, spect_stream stream);
+
+/*
+ * spect_back -- x = A' v (Algorithm 2), the exact transpose of
+ * spect_forward (Eq. (2)); the adjoint of the rotation is the transpose of
+ * the bilinear interpolation, not a rotation by -theta (Section II-A).
+ *   v  device, nx*nz*nview, read only.
+ *   x  device, nx*ny*nz, overwritten (not accumulated).
+ * Errors as spect_forward.
+ */
+spect_status spect_back(spect_plan plan, const float* v, float* x, spect_stream stream);
+
+/*
+ * spect_em_step -- niter MLEM updates (Eqs. (7)-(8) with beta = 0):
+ *   x <- x * A'(y / (A x + rbar)) / A'1, in place.
+ *   x     device, nx*ny*nz, non-negative; updated in place.
+ *   y     device, nx*nz*nview measured counts, read only.
+ *   rbar  device, nx*nz*nview background means, or NULL for zero.
+ *   niter >= 0 (0 is a no-op).
+ * Guards (not stated in the paper): where A x + rbar <= 0 the ratio is 0;
+ * where A'1 <= 0 the voxel is set to 0.  The sensitivity A'1 is computed on
+ * the first call and cached in the plan.
+ * Errors as spect_forward; SPECT_EINVAL for niter < 0.
+ */
+spect_status spect_em_step(spect_plan plan, float* x, const float* y, const float* rbar,
+                           int niter, spect_stream stream);
+
+/*
+ * spect_sensitivity -- copy the plan's sensitivity s = A'1 (the d(0) term
+ * of Eq. (8)) into s (device, nx*ny*nz).  Computes and caches it first if
+ * needed.  Errors as spect_forward.
+ */
+spect_status spect_sensitivity(spect_plan plan, float* s, spect_stream stream);
+
+/*
+ * spect_plan_info -- describe a plan (host out-pointers; any may be NULL):
+ *   separable   1 when the separable-factor kernels are used, else 0.
+ *   view_chunk  views processed per pass through the work slab.
+ *   device_bytes device memory held by the plan (state + work slab).
+ */
+spect_status spect_plan_info(spect_plan plan, int* separable, int* view_chunk, size_t* device_bytes);
+
+/* Kernel classes for spect_profile_read(). */
+enum {
+    SPECT_K_ROTATE_ATTEN = 0, /* rotate x, mu; Eq. (1) attenuation            */
+    SPECT_K_CONV_FWD = 1,     /* PSF blur + depth sum (+ EM ratio)            */
+    SPECT_K_CONV_ADJ = 2,     /* PSF blur adjoint + attenuation               */
+    SPECT_K_ROTATE_ADJ = 3,   /* adjoint rotation + view sum (+ EM update)    */
+    SPECT_K_OTHER = 4,        /* fills and set-up work                        */
+    SPECT_K_COUNT = 5
+};
+
+/*
+ * spect_profile_enable -- when enable != 0, every later kernel launch of the
+ * plan is bracketed by a pair of CUDA events recorded on the launch stream,
+ * so its device duration can be read back.  Costs two event records per
+ * launch; off by default.  Launch counting is always on.
+ */
+spect_status spect_profile_enable(spect_plan plan, int enable);
+
+/*
+ * spect_profile_read -- per kernel class (SPECT_K_*), the number of kernel
+ * launches since the last reset (launches[SPECT_K_COUNT], host) and the summed
+ * device milliseconds of the launches made while profiling was enabled
+ * (ms[SPECT_K_COUNT], host; synchronises on the recorded events).  Either
+ * pointer may be NULL.  With reset != 0 the counters restart from zero.
+ */
+spect_status spect_profile_read(spect_plan plan, long long* launches, double* ms, int reset);
+
+/* spect_plan_destroy -- release the plan; NULL is accepted and returns OK.
+ * Waits for the plan's outstanding work on the device before freeing. */
+spect_status spect_plan_destroy(spect_plan plan);
+
+/* Thread-local message for the last non-OK status returned on this thread
+ * ("" if none).  The pointer stays valid until the next call on the thread. */
+const char* spect_last_error(void);
+
+/* Library version string, e.g. "spect-gb300 0.1 (sm_103a)". */
+const char* spect_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPECT_H */

@@ -1,0 +1,467 @@
+// plan.cu -- the C ABI (include/spect.h): plan construction, argument
+// validation, and the stream-ordered orchestration of the kernels for
+// A (Algorithm 1), A' (Algorithm 2) and the MLEM update (Eqs. (7)-(8), beta=0).
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <string>
+#include <vector>
+
+#include "spect_internal.cuh"
+
+using spect::Geometry;
+using spect::ViewRot;
+
+namespace {
+
+thread_local std::string g_err;
+
+spect_status fail(spect_status st, const std::string& msg)
+{
+    g_err = msg;
+    return st;
+}
+
+#define SPECT_CUDA_TRY(expr, what)                                                        \
+    do {                                                                                  \
+        cudaError_t e_ = (expr);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(SPECT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// cos/sin with exact values at multiples of pi/2 (the rotation of a quarter
+// turn is then an exact lattice permutation).
+void exact_cos_sin(double th, double* c, double* s)
+{
+    const double q = th / (M_PI / 2.0);
+    const double r = nearbyint(q);
+    if (fabs(q - r) < 1e-12) {
+        const long m = (((long)r % 4) + 4) % 4;
+        *c = (m == 0) ? 1.0 : (m == 2 ? -1.0 : 0.0);
+        *s = (m == 1) ? 1.0 : (m == 3 ? -1.0 : 0.0);
+    } else {
+        *c = cos(th);
+        *s = sin(th);
+    }
+}
+
+// Split t = hi + lo with hi a multiple of 2^-h (see rot_sample()).
+void split(double t, int h, float* hi, float* lo)
+{
+    const double sc = ldexp(1.0, h);
+    const double th = nearbyint(t * sc) / sc;
+    *hi = (float)th;
+    *lo = (float)(t - th);
+}
+
+template <class T>
+spect_status dalloc(spect_plan_s* P, T** p, size_t count, const char* what)
+{
+    *p = nullptr;
+    if (count == 0) return SPECT_OK;
+    const size_t bytes = count * sizeof(T);
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? SPECT_ENOMEM : SPECT_ECUDA,
+                    std::string("allocating ") + what + ": " + cudaGetErrorString(e));
+    }
+    P->bytes += bytes;
+    return SPECT_OK;
+}
+
+void free_plan(spect_plan_s* P)
+{
+    if (!P) return;
+    for (auto& p : P->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (cudaEvent_t e : P->evpool) cudaEventDestroy(e);
+    void* ptrs[] = {P->mu, P->psf, P->psf_adj, P->fx, P->fz, P->fx_adj, P->fz_adj, P->rot,
+                    P->adj_off, P->adj, P->slab, P->e, P->ratio, P->s};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete P;
+}
+
+size_t slab_budget_bytes()
+{
+    // Work slab size: chosen so a chunk of views stays resident in L2 by
+    // default; SPECT_SLAB_MB overrides (tuning).
+    const char* env = getenv("SPECT_SLAB_MB");
+    long mb = env ? atol(env) : 256;
+    if (mb < 1) mb = 1;
+    return (size_t)mb << 20;
+}
+
+cudaEvent_t pool_event(spect_plan_s* P)
+{
+    if (!P->evpool.empty()) {
+        cudaEvent_t e = P->evpool.back();
+        P->evpool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Count a launch of kernel class `kind`; when profiling, bracket it with events.
+template <class F>
+cudaError_t counted(spect_plan_s* P, int kind, cudaStream_t st, F&& launch)
+{
+    P->launches[kind] += 1;
+    if (!P->prof) return launch();
+    cudaEvent_t a = pool_event(P), b = pool_event(P);
+    if (!a || !b) return cudaErrorMemoryAllocation;
+    cudaEventRecord(a, st);
+    cudaError_t e = launch();
+    cudaEventRecord(b, st);
+    P->pending.push_back({kind, a, b});
+    return e;
+}
+
+cudaError_t drain_profile(spect_plan_s* P)
+{
+    cudaError_t err = cudaSuccess;
+    for (auto& p : P->pending) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(p.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.a, p.b);
+        if (e != cudaSuccess) err = e;
+        else P->prof_ms[p.kind] += ms;
+        P->evpool.push_back(p.a);
+        P->evpool.push_back(p.b);
+    }
+    P->pending.clear();
+    return err;
+}
+
+spect_status run_forward(spect_plan_s* P, const float* x, float* v, const float* y, const float* rbar,
+                         cudaStream_t st)
+{
+    const int nview = P->g.nview;
+    for (int l0 = 0; l0 < nview; l0 += P->chunk) {
+        const int nv = std::min(P->chunk, nview - l0);
+        SPECT_CUDA_TRY(counted(P, SPECT_K_ROTATE_ATTEN, st, [&] { return spect::launch_rotate_atten(*P, x, l0, nv, st); }),
+                       "rotate/attenuate launch");
+        SPECT_CUDA_TRY(counted(P, SPECT_K_CONV_FWD, st,
+                               [&] { return spect::launch_conv_forward(*P, v, l0, nv, y, rbar, st); }),
+                       "PSF blur launch");
+    }
+    return SPECT_OK;
+}
+
+// out = A' v; with em_x set, the last chunk writes x <- x * out / s into em_x instead.
+spect_status run_back(spect_plan_s* P, const float* v, float* out, float* em_x, const float* em_s, cudaStream_t st)
+{
+    const int nview = P->g.nview;
+    for (int l0 = 0; l0 < nview; l0 += P->chunk) {
+        const int nv = std::min(P->chunk, nview - l0);
+        const bool last = l0 + nv >= nview;
+        SPECT_CUDA_TRY(counted(P, SPECT_K_CONV_ADJ, st, [&] { return spect::launch_conv_adjoint(*P, v, l0, nv, st); }),
+                       "PSF blur adjoint launch");
+        float* emx = (last && em_x) ? em_x : nullptr;
+        SPECT_CUDA_TRY(counted(P, SPECT_K_ROTATE_ADJ, st,
+                               [&] { return spect::launch_rotate_adjoint(*P, l0, nv, out, l0 > 0, emx, em_s, emx, st); }),
+                       "adjoint rotation launch");
+    }
+    return SPECT_OK;
+}
+
+spect_status ensure_sensitivity(spect_plan_s* P, cudaStream_t st)
+{
+    if (P->s_valid) return SPECT_OK;
+    const size_t nproj = (size_t)P->g.nx * P->g.nz * P->g.nview;
+    SPECT_CUDA_TRY(counted(P, SPECT_K_OTHER, st, [&] { return spect::launch_fill(P->ratio, nproj, 1.f, st); }),
+                   "fill launch");
+    spect_status r = run_back(P, P->ratio, P->s, nullptr, nullptr, st);
+    if (r != SPECT_OK) return r;
+    P->s_valid = 1;
+    return SPECT_OK;
+}
+
+spect_status check_call(spect_plan P, const void* a, const void* b, const char* na, const char* nb)
+{
+    if (!P) return fail(SPECT_EINVAL, "plan is NULL");
+    if (!a) return fail(SPECT_EINVAL, std::string(na) + " is NULL");
+    if (!b) return fail(SPECT_EINVAL, std::string(nb) + " is NULL");
+    if (!aligned16(a)) return fail(SPECT_EINVAL, std::string(na) + " is not 16-byte aligned");
+    if (!aligned16(b)) return fail(SPECT_EINVAL, std::string(nb) + " is not 16-byte aligned");
+    return SPECT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* spect_last_error(void) { return g_err.c_str(); }
+
+const char* spect_version(void) { return "spect-gb300 0.1 (sm_103a)"; }
+
+spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nview, const float* mu, float dy,
+                               const float* psf, const float* psf_fx, const float* psf_fz, int px, int pz,
+                               int nview_psf, const double* angles, unsigned flags, spect_stream stream)
+{
+    if (!out) return fail(SPECT_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nx != ny) return fail(SPECT_EINVAL, "nx must equal ny (rotation in the x-y plane)");
+    if (nx < 2 || nx > 1024) return fail(SPECT_EINVAL, "nx must be in [2, 1024]");
+    if (nz < 1 || nz > 4096) return fail(SPECT_EINVAL, "nz must be in [1, 4096]");
+    if (nview < 1 || nview > 4096) return fail(SPECT_EINVAL, "nview must be in [1, 4096]");
+    if (px < 1 || pz < 1 || px > 127 || pz > 127 || (px % 2) == 0 || (pz % 2) == 0)
+        return fail(SPECT_EINVAL, "PSF sizes px, pz must be odd and in [1, 127]");
+    if (nview_psf != 1 && nview_psf != nview) return fail(SPECT_EINVAL, "nview_psf must be 1 or nview");
+    if (!(dy >= 0.f) || !isfinite(dy)) return fail(SPECT_EINVAL, "dy must be finite and >= 0");
+    if ((psf_fx == nullptr) != (psf_fz == nullptr)) return fail(SPECT_EINVAL, "give both psf_fx and psf_fz or neither");
+    if (!psf && !psf_fx) return fail(SPECT_EINVAL, "no PSF given (psf or psf_fx/psf_fz)");
+    if ((flags & ~(unsigned)SPECT_PLAN_PREFER_SEPARABLE) != 0) return fail(SPECT_EINVAL, "unknown flag bits");
+    const void* ins[] = {mu, psf, psf_fx, psf_fz};
+    for (const void* p : ins)
+        if (p && !aligned16(p)) return fail(SPECT_EINVAL, "device inputs must be 16-byte aligned");
+    if ((size_t)nview * nx * ny * 6 >= (size_t)INT32_MAX) return fail(SPECT_EUNSUPPORTED, "nview*nx*ny too large");
+    if (angles)
+        for (int l = 0; l < nview; ++l)
+            if (!isfinite(angles[l])) return fail(SPECT_EINVAL, "angles must be finite");
+
+    cudaStream_t st = (cudaStream_t)stream;
+    spect_plan_s* P = new spect_plan_s();
+    Geometry& g = P->g;
+    g.nx = nx; g.ny = ny; g.nz = nz; g.nview = nview;
+    g.px = px; g.pz = pz; g.nvp = nview_psf;
+    g.cint = (nx - 1) / 2;
+    g.cfrac = (nx - 1) % 2 ? 0.5f : 0.f;
+    g.dy = dy;
+    g.has_mu = mu != nullptr;
+    P->separable = psf_fx && (!psf || (flags & SPECT_PLAN_PREFER_SEPARABLE));
+    P->cls_x = 3;
+    P->cls_z = nz >= 2 ? 3 : 1;
+
+    int dev = 0, smem_optin = 0;
+    spect_status r = SPECT_OK;
+#define PLAN_TRY(expr, what)                                                                  \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            free_plan(P);                                                                     \
+            return fail(SPECT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e_));     \
+        }                                                                                     \
+    } while (0)
+#define PLAN_ALLOC(ptr, n, what)                           \
+    do {                                                   \
+        r = dalloc(P, &(ptr), (n), what);                  \
+        if (r != SPECT_OK) {                               \
+            std::string m_ = g_err;                        \
+            free_plan(P);                                  \
+            return fail(r, m_);                            \
+        }                                                  \
+    } while (0)
+
+    PLAN_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    PLAN_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "device query");
+    if (P->separable) {
+        P->sep_tk = spect::choose_sep_tile(g, P->cls_z, (size_t)smem_optin);
+        if (P->sep_tk < 1) {
+            free_plan(P);
+            return fail(SPECT_EUNSUPPORTED, "separable PSF tile does not fit shared memory for this nx, pz");
+        }
+    } else if (!spect::direct_fits(g, (size_t)smem_optin)) {
+        free_plan(P);
+        return fail(SPECT_EUNSUPPORTED, "full PSF tile does not fit shared memory");
+    }
+
+    const size_t vol = (size_t)nx * ny * nz, nproj = (size_t)nx * nz * nview;
+    const size_t nxy = (size_t)nx * ny, nrows = (size_t)nview_psf * ny;
+
+    // attenuation map (zeros are never read when mu == NULL)
+    PLAN_ALLOC(P->mu, vol, "mu");
+    if (mu) PLAN_TRY(cudaMemcpyAsync(P->mu, mu, vol * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy mu");
+    else PLAN_TRY(cudaMemsetAsync(P->mu, 0, vol * sizeof(float), st), "clear mu");
+
+    // PSF and its edge-class variants for A'
+    if (P->separable) {
+        PLAN_ALLOC(P->fx, (size_t)px * nrows, "psf_fx");
+        PLAN_ALLOC(P->fz, (size_t)pz * nrows, "psf_fz");
+        PLAN_ALLOC(P->fx_adj, (size_t)3 * px * nrows, "psf_fx variants");
+        PLAN_ALLOC(P->fz_adj, (size_t)P->cls_z * pz * nrows, "psf_fz variants");
+        PLAN_TRY(cudaMemcpyAsync(P->fx, psf_fx, (size_t)px * nrows * sizeof(float), cudaMemcpyDeviceToDevice, st),
+                 "copy psf_fx");
+        PLAN_TRY(cudaMemcpyAsync(P->fz, psf_fz, (size_t)pz * nrows * sizeof(float), cudaMemcpyDeviceToDevice, st),
+                 "copy psf_fz");
+        PLAN_TRY(spect::launch_psf_variants(*P, nullptr, st), "PSF variant launch");
+    } else {
+        const size_t n = (size_t)px * pz * nrows;
+        PLAN_ALLOC(P->psf, n, "psf");
+        PLAN_ALLOC(P->psf_adj, n * P->cls_x * P->cls_z, "psf variants");
+        PLAN_TRY(cudaMemcpyAsync(P->psf, psf, n * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy psf");
+        float* scratch = nullptr;
+        PLAN_TRY(cudaMalloc((void**)&scratch, n * P->cls_x * sizeof(float)), "PSF variant scratch");
+        cudaError_t e1 = spect::launch_psf_variants(*P, scratch, st);
+        cudaError_t e2 = cudaStreamSynchronize(st);
+        cudaFree(scratch);
+        PLAN_TRY(e1, "PSF variant launch");
+        PLAN_TRY(e2, "PSF variant build");
+    }
+
+    // per-view rotation constants
+    {
+        int lg = 0;
+        while ((1 << lg) < nx) ++lg;
+        const int h = 22 - lg;
+        std::vector<ViewRot> vr(nview);
+        for (int l = 0; l < nview; ++l) {
+            const double th = angles ? angles[l] : 2.0 * M_PI * (double)l / (double)nview;
+            double c, s;
+            exact_cos_sin(th, &c, &s);
+            split(c, h, &vr[l].ct_hi, &vr[l].ct_lo);
+            split(s, h, &vr[l].st_hi, &vr[l].st_lo);
+        }
+        PLAN_ALLOC(P->rot, (size_t)nview, "rotation constants");
+        PLAN_TRY(cudaMemcpyAsync(P->rot, vr.data(), nview * sizeof(ViewRot), cudaMemcpyHostToDevice, st),
+                 "upload rotation constants");
+        PLAN_TRY(cudaStreamSynchronize(st), "rotation constants");
+    }
+
+    // adjacency lists of the transposed rotation (count, scan on host, fill)
+    {
+        const size_t nlist = nxy * nview;
+        int* d_counts = nullptr;
+        int* d_max = nullptr;
+        PLAN_TRY(cudaMalloc((void**)&d_counts, nlist * sizeof(int)), "adjacency counts");
+        PLAN_TRY(cudaMalloc((void**)&d_max, sizeof(int)), "adjacency max");
+        cudaMemsetAsync(d_max, 0, sizeof(int), st);
+        cudaError_t e1 = spect::launch_build_adjacency(*P, 0, d_counts, d_max, st);
+        std::vector<int> counts(nlist);
+        int mx = 0;
+        cudaError_t e2 = cudaMemcpyAsync(counts.data(), d_counts, nlist * sizeof(int), cudaMemcpyDeviceToHost, st);
+        cudaError_t e3 = cudaMemcpyAsync(&mx, d_max, sizeof(int), cudaMemcpyDeviceToHost, st);
+        cudaError_t e4 = cudaStreamSynchronize(st);
+        cudaFree(d_counts);
+        cudaFree(d_max);
+        PLAN_TRY(e1, "adjacency count launch");
+        PLAN_TRY(e2, "adjacency counts download");
+        PLAN_TRY(e3, "adjacency max download");
+        PLAN_TRY(e4, "adjacency count");
+        std::vector<int> off(nlist + 1);
+        size_t tot = 0;
+        for (size_t m = 0; m < nlist; ++m) {
+            off[m] = (int)tot;
+            tot += (size_t)counts[m];
+        }
+        off[nlist] = (int)tot;
+        P->adj_max = mx;
+        PLAN_ALLOC(P->adj_off, nlist + 1, "adjacency offsets");
+        PLAN_ALLOC(P->adj, std::max<size_t>(tot, 1), "adjacency entries");
+        PLAN_TRY(cudaMemcpyAsync(P->adj_off, off.data(), (nlist + 1) * sizeof(int), cudaMemcpyHostToDevice, st),
+                 "upload adjacency offsets");
+        PLAN_TRY(spect::launch_build_adjacency(*P, 1, nullptr, nullptr, st), "adjacency fill launch");
+        PLAN_TRY(cudaStreamSynchronize(st), "adjacency fill");
+    }
+
+    // work slab and EM buffers
+    const size_t budget = slab_budget_bytes();
+    P->chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)nview, budget / (vol * sizeof(float))));
+    PLAN_ALLOC(P->slab, vol * (size_t)P->chunk, "work slab");
+    PLAN_ALLOC(P->e, vol, "EM accumulator");
+    PLAN_ALLOC(P->ratio, nproj, "EM ratio");
+    PLAN_ALLOC(P->s, vol, "sensitivity");
+    PLAN_TRY(cudaStreamSynchronize(st), "plan set-up");
+    *out = P;
+    return SPECT_OK;
+#undef PLAN_TRY
+#undef PLAN_ALLOC
+}
+
+spect_status spect_plan_destroy(spect_plan P)
+{
+    if (!P) return SPECT_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    free_plan(P);
+    if (e != cudaSuccess) return fail(SPECT_ECUDA, std::string("synchronise before destroy: ") + cudaGetErrorString(e));
+    return SPECT_OK;
+}
+
+spect_status spect_forward(spect_plan P, const float* x, float* v, spect_stream stream)
+{
+    spect_status r = check_call(P, x, v, "x", "v");
+    if (r != SPECT_OK) return r;
+    return run_forward(P, x, v, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+spect_status spect_back(spect_plan P, const float* v, float* x, spect_stream stream)
+{
+    spect_status r = check_call(P, v, x, "v", "x");
+    if (r != SPECT_OK) return r;
+    return run_back(P, v, x, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+spect_status spect_sensitivity(spect_plan P, float* s, spect_stream stream)
+{
+    spect_status r = check_call(P, s, s, "s", "s");
+    if (r != SPECT_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    r = ensure_sensitivity(P, st);
+    if (r != SPECT_OK) return r;
+    const size_t vol = (size_t)P->g.nx * P->g.ny * P->g.nz;
+    SPECT_CUDA_TRY(cudaMemcpyAsync(s, P->s, vol * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy sensitivity");
+    return SPECT_OK;
+}
+
+spect_status spect_em_step(spect_plan P, float* x, const float* y, const float* rbar, int niter, spect_stream stream)
+{
+    spect_status r = check_call(P, x, y, "x", "y");
+    if (r != SPECT_OK) return r;
+    if (rbar && !aligned16(rbar)) return fail(SPECT_EINVAL, "rbar is not 16-byte aligned");
+    if (niter < 0) return fail(SPECT_EINVAL, "niter must be >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    r = ensure_sensitivity(P, st);
+    if (r != SPECT_OK) return r;
+    for (int it = 0; it < niter; ++it) {
+        r = run_forward(P, x, P->ratio, y, rbar, st);
+        if (r != SPECT_OK) return r;
+        r = run_back(P, P->ratio, P->e, x, P->s, st);
+        if (r != SPECT_OK) return r;
+    }
+    return SPECT_OK;
+}
+
+spect_status spect_profile_enable(spect_plan P, int enable)
+{
+    if (!P) return fail(SPECT_EINVAL, "plan is NULL");
+    P->prof = enable != 0;
+    return SPECT_OK;
+}
+
+spect_status spect_profile_read(spect_plan P, long long* launches, double* ms, int reset)
+{
+    if (!P) return fail(SPECT_EINVAL, "plan is NULL");
+    cudaError_t e = drain_profile(P);
+    for (int k = 0; k < SPECT_K_COUNT; ++k) {
+        if (launches) launches[k] = P->launches[k];
+        if (ms) ms[k] = P->prof_ms[k];
+        if (reset) {
+            P->launches[k] = 0;
+            P->prof_ms[k] = 0.0;
+        }
+    }
+    if (e != cudaSuccess) return fail(SPECT_ECUDA, std::string("reading kernel timings: ") + cudaGetErrorString(e));
+    return SPECT_OK;
+}
+
+spect_status spect_plan_info(spect_plan P, int* separable, int* view_chunk, size_t* device_bytes)
+{
+    if (!P) return fail(SPECT_EINVAL, "plan is NULL");
+    if (separable) *separable = P->separable;
+    if (view_chunk) *view_chunk = P->chunk;
+    if (device_bytes) *device_bytes = P->bytes;
+    return SPECT_OK;
+}
+
+}  // extern "C"

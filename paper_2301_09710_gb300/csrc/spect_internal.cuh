@@ -1,0 +1,191 @@
+// spect_internal.cuh -- plan state, device helpers and kernel launchers shared
+// by the translation units of the sm_103a SPECT projector library.
+//
+// Operator (Section II-A of arXiv 2301.09710, Algorithms 1 and 2):
+//   A : rotate x and mu by theta_l (bilinear, zero padding), weight by the
+//       Eq. (1) accumulated attenuation, blur every depth plane j with
+//       p(:,:,j,l) (convolution, replicate padding), sum over depth.
+//   A': the exact transpose of every step, in gather (owner-computes) form.
+//
+// Work layout.  Views are processed in chunks of `chunk` views through one
+// work slab of chunk * nx*ny*nz floats laid out [v][k][j][i] (i fastest):
+// row (k, j) of view v is contiguous, plane (i, j) of slice k is contiguous.
+//   forward : K1 rotate+attenuate  x -> slab (w)      then K2 blur+depth-sum slab -> v
+//   back    : K2T blur-adjoint+attenuate v -> slab (t) then K1T adjoint-rotate+view-sum slab -> x
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/spect.h"
+
+namespace spect {
+
+// Per-view rotation constants.  cos/sin are split as hi + lo with hi a
+// multiple of 2^-h (h chosen per plan) so that hi * (i - c) + hi' * (j - c)
+// is exact in FP32; the fractional sample offset is then formed without
+// ever rounding the (large) sample coordinate itself.  See rot_sample().
+struct ViewRot {
+    float ct_hi, ct_lo, st_hi, st_lo;
+};
+
+struct Geometry {
+    int nx, ny, nz, nview;
+    int px, pz, nvp;  // PSF size and number of PSF views (1 or nview)
+    int cint;         // floor((nx-1)/2)
+    float cfrac;      // (nx-1)/2 - cint  (0 or 0.5)
+    float dy;
+    int has_mu;
+};
+
+// One adjacency entry of the transposed rotation: source pixel p (i + nx*j
+// in the rotated frame) and its bilinear weight on the destination voxel.
+struct AdjEntry {
+    int p;
+    float w;
+};
+
+}  // namespace spect
+
+struct spect_plan_s {
+    spect::Geometry g;
+    int separable;
+    int chunk;            // views per slab pass
+    int adj_max;          // longest adjacency list
+    // device state owned by the plan
+    float* mu = nullptr;         // nx*ny*nz
+    float* psf = nullptr;        // direct: px*pz*ny*nvp
+    float* psf_adj = nullptr;    // direct: nvar * px*pz*ny*nvp edge-class variants for A'
+    float* fx = nullptr;         // separable: px*ny*nvp
+    float* fz = nullptr;         // separable: pz*ny*nvp
+    float* fx_adj = nullptr;     // separable: cls_x * px*ny*nvp
+    float* fz_adj = nullptr;     // separable: cls_z * pz*ny*nvp
+    spect::ViewRot* rot = nullptr;  // nview
+    int* adj_off = nullptr;      // nview*nx*ny + 1
+    spect::AdjEntry* adj = nullptr;
+    float* slab = nullptr;       // chunk * nx*ny*nz
+    float* e = nullptr;          // nx*ny*nz  (EM back-projection accumulator)
+    float* ratio = nullptr;      // nx*nz*nview (EM ratio / ones)
+    float* s = nullptr;          // nx*ny*nz  (sensitivity A'1)
+    int s_valid = 0;
+    int cls_x = 3, cls_z = 3;    // edge classes per axis for A' (1 when the axis has length 1)
+    int sep_tk = 0;              // separable kernels: k-rows per block
+    size_t bytes = 0;
+    // launch accounting and optional per-launch event timing
+    long long launches[SPECT_K_COUNT] = {0, 0, 0, 0, 0};
+    double prof_ms[SPECT_K_COUNT] = {0, 0, 0, 0, 0};
+    int prof = 0;
+    struct Pending { int kind; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> evpool;
+};
+
+namespace spect {
+
+// --------------------------------------------------------------------- device helpers
+// Bilinear sample of rotated-frame pixel (i, j): integer corner (i0, j0) and
+// fractional offsets (fx, fy) in [0,1], computed identically by A, by the
+// adjacency builder of A', and by the attenuation passes, so the weights of
+// A and A' are bitwise the same.  Intrinsics forbid FMA contraction.
+struct Sample {
+    int i0, j0;
+    float fx, fy;
+};
+
+__device__ __forceinline__ Sample rot_sample(int i, int j, const ViewRot r, int cint, float cfrac)
+{
+    // d = index - c, exact (half-)integers
+    const float di = __fsub_rn(__fsub_rn((float)i, (float)cint), cfrac);
+    const float dj = __fsub_rn(__fsub_rn((float)j, (float)cint), cfrac);
+    // exact parts (hi multiples of 2^-h times small half-integers)
+    const float ax = __fadd_rn(__fmul_rn(r.ct_hi, di), __fmul_rn(r.st_hi, dj));
+    const float ay = __fsub_rn(__fmul_rn(r.ct_hi, dj), __fmul_rn(r.st_hi, di));
+    // small residuals
+    const float rx = __fadd_rn(__fmul_rn(r.ct_lo, di), __fmul_rn(r.st_lo, dj));
+    const float ry = __fsub_rn(__fmul_rn(r.ct_lo, dj), __fmul_rn(r.st_lo, di));
+    const float tx = __fadd_rn(ax, cfrac);  // exact
+    const float ty = __fadd_rn(ay, cfrac);
+    const float flx = floorf(tx), fly = floorf(ty);
+    float fx = __fadd_rn(__fsub_rn(tx, flx), rx);
+    float fy = __fadd_rn(__fsub_rn(ty, fly), ry);
+    int i0 = (int)flx + cint, j0 = (int)fly + cint;
+    if (fx < 0.f) { fx = __fadd_rn(fx, 1.f); i0 -= 1; }
+    else if (fx >= 1.f) { fx = __fsub_rn(fx, 1.f); i0 += 1; }
+    if (fy < 0.f) { fy = __fadd_rn(fy, 1.f); j0 -= 1; }
+    else if (fy >= 1.f) { fy = __fsub_rn(fy, 1.f); j0 += 1; }
+    Sample s;
+    s.i0 = i0; s.j0 = j0; s.fx = fx; s.fy = fy;
+    return s;
+}
+
+// Weight of corner (di, dj) in {0,1}^2 of a bilinear sample.
+__device__ __forceinline__ float bilinear_w(const Sample& s, int di, int dj)
+{
+    const float wx = di ? s.fx : __fsub_rn(1.f, s.fx);
+    const float wy = dj ? s.fy : __fsub_rn(1.f, s.fy);
+    return __fmul_rn(wx, wy);
+}
+
+// Bilinear gather from one nx*ny slice with zero padding (Section II-A).
+__device__ __forceinline__ float gather_bilinear(const float* __restrict__ sl, const Sample& s, int nx, int ny)
+{
+    const bool vi0 = (unsigned)s.i0 < (unsigned)nx, vi1 = (unsigned)(s.i0 + 1) < (unsigned)nx;
+    const bool vj0 = (unsigned)s.j0 < (unsigned)ny, vj1 = (unsigned)(s.j0 + 1) < (unsigned)ny;
+    const float* row0 = sl + (ptrdiff_t)s.j0 * nx + s.i0;
+    const float* row1 = row0 + nx;
+    float acc = 0.f;
+    if (vj0 && vi0) acc = __fmaf_rn(bilinear_w(s, 0, 0), __ldg(row0), acc);
+    if (vj0 && vi1) acc = __fmaf_rn(bilinear_w(s, 1, 0), __ldg(row0 + 1), acc);
+    if (vj1 && vi0) acc = __fmaf_rn(bilinear_w(s, 0, 1), __ldg(row1), acc);
+    if (vj1 && vi1) acc = __fmaf_rn(bilinear_w(s, 1, 1), __ldg(row1 + 1), acc);
+    return acc;
+}
+
+// Running Eq. (1) attenuation along depth, from the detector side (j = ny-1)
+// inwards: S = sum_{s>j} mu~(s) kept with Kahan compensation.
+struct AttenScan {
+    float S = 0.f, c = 0.f;
+    // mubar(j) = exp(-dy (mu~(j)/2 + S)), then S += mu~(j)
+    __device__ __forceinline__ float step(float m, float dy)
+    {
+        const float half = 0.5f * m - c;
+        const float mb = expf(-dy * (S + half));
+        const float y = m - c;
+        const float t = S + y;
+        c = (t - S) - y;
+        S = t;
+        return mb;
+    }
+};
+
+// Kahan-compensated accumulator for depth and view sums.
+struct KSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ float value() const { return s - c; }
+};
+
+// --------------------------------------------------------------------- launchers
+// All return the cudaError_t of the launch (cudaGetLastError()).
+cudaError_t launch_build_adjacency(const spect_plan_s& P, int pass, int* counts, int* maxcount, cudaStream_t st);
+cudaError_t launch_rotate_atten(const spect_plan_s& P, const float* x, int l0, int nv, cudaStream_t st);
+cudaError_t launch_rotate_adjoint(const spect_plan_s& P, int l0, int nv, float* out, int accumulate,
+                                  const float* em_x, const float* em_s, float* em_xout, cudaStream_t st);
+cudaError_t launch_conv_forward(const spect_plan_s& P, float* v, int l0, int nv, const float* em_y,
+                                const float* em_rbar, cudaStream_t st);
+cudaError_t launch_conv_adjoint(const spect_plan_s& P, const float* v, int l0, int nv, cudaStream_t st);
+cudaError_t launch_psf_variants(spect_plan_s& P, float* scratch, cudaStream_t st);
+int choose_sep_tile(const Geometry& g, int cls_z, size_t smem_limit);
+bool direct_fits(const Geometry& g, size_t smem_limit);
+cudaError_t launch_fill(float* p, size_t n, float value, cudaStream_t st);
+
+}  // namespace spect

@@ -1,0 +1,157 @@
+"""Python front end of the C ABI: a plan object over torch CUDA tensors.
+
+Tensor layouts (C order, float32, contiguous, on the plan's CUDA device):
+  x, mu : (nz, ny, nx)             x(i,j,k) = x[k, j, i]
+  v, y  : (nview, nz, nx)          v(i,k,l) = v[l, k, i]
+  psf   : (nview_psf, ny, pz, px)  p(a,b,j,l) = psf[l, j, b, a]
+  fx    : (nview_psf, ny, px),  fz : (nview_psf, ny, pz)   p = fx (x) fz
+
+Every method is argument marshalling around one C call (``include/spect.h``);
+the work runs in the library's kernels on the current torch stream (or the
+stream passed in).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+def _as_dev(t, device) -> torch.Tensor:
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        t = torch.from_numpy(np.ascontiguousarray(np.asarray(t, dtype=np.float32)))
+    return t.to(device=device, dtype=torch.float32).contiguous()
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream_handle(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class SpectPlan:
+    """The operator A of one geometry (Algorithm 1 inputs) on one GPU."""
+
+    def __init__(self, nx: int, nz: int, nview: int, mu=None, dy: float = 1.0, psf=None, fx=None, fz=None,
+                 angles=None, prefer_separable: bool = True, device=None, stream=None):
+        self.lib = _lib.load()
+        self.device = torch.device(device if device is not None else "cuda")
+        self.nx = self.ny = int(nx)
+        self.nz, self.nview = int(nz), int(nview)
+        self._mu = _as_dev(mu, self.device)
+        self._psf = _as_dev(psf, self.device)
+        self._fx = _as_dev(fx, self.device)
+        self._fz = _as_dev(fz, self.device)
+        if self._psf is not None:
+            nvp, _, pz, px = self._psf.shape
+        else:
+            nvp, _, px = self._fx.shape
+            pz = self._fz.shape[-1]
+        self.px, self.pz, self.nview_psf = int(px), int(pz), int(nvp)
+        ang = None
+        if angles is not None:
+            self._angles = np.ascontiguousarray(np.asarray(angles, dtype=np.float64))
+            ang = self._angles.ctypes.data_as(ctypes.c_void_p)
+        handle = ctypes.c_void_p()
+        flags = _lib.SPECT_PLAN_PREFER_SEPARABLE if prefer_separable else 0
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.spect_plan_create(
+                ctypes.byref(handle), self.nx, self.ny, self.nz, self.nview, _ptr(self._mu), ctypes.c_float(dy),
+                _ptr(self._psf), _ptr(self._fx), _ptr(self._fz), self.px, self.pz, self.nview_psf, ang, flags,
+                _stream_handle(stream)))
+        self.handle = handle
+        # the plan holds its own copies
+        self._mu = self._psf = self._fx = self._fz = None
+
+    # ------------------------------------------------------------------ shapes
+    @property
+    def vol_shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def proj_shape(self):
+        return (self.nview, self.nz, self.nx)
+
+    def _check(self, t, shape, name):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+    # ------------------------------------------------------------------ ops
+    def forward(self, x, out=None, stream=None) -> torch.Tensor:
+        """v = A x (Algorithm 1)."""
+        self._check(x, self.vol_shape, "x")
+        if out is None:
+            out = torch.empty(self.proj_shape, device=x.device, dtype=torch.float32)
+        self._check(out, self.proj_shape, "out")
+        _lib.check(self.lib.spect_forward(self.handle, _ptr(x), _ptr(out), _stream_handle(stream)))
+        return out
+
+    def back(self, v, out=None, stream=None) -> torch.Tensor:
+        """x = A' v (Algorithm 2), the exact transpose of forward()."""
+        self._check(v, self.proj_shape, "v")
+        if out is None:
+            out = torch.empty(self.vol_shape, device=v.device, dtype=torch.float32)
+        self._check(out, self.vol_shape, "out")
+        _lib.check(self.lib.spect_back(self.handle, _ptr(v), _ptr(out), _stream_handle(stream)))
+        return out
+
+    def em_step(self, x, y, rbar=None, niter: int = 1, stream=None) -> torch.Tensor:
+        """niter in-place MLEM updates x <- x A'(y/(Ax+rbar)) / A'1 (Eqs. (7)-(8), beta = 0)."""
+        self._check(x, self.vol_shape, "x")
+        self._check(y, self.proj_shape, "y")
+        if rbar is not None:
+            self._check(rbar, self.proj_shape, "rbar")
+        _lib.check(self.lib.spect_em_step(self.handle, _ptr(x), _ptr(y), _ptr(rbar), int(niter),
+                                          _stream_handle(stream)))
+        return x
+
+    def sensitivity(self, stream=None) -> torch.Tensor:
+        """s = A' 1."""
+        s = torch.empty(self.vol_shape, device=self.device, dtype=torch.float32)
+        _lib.check(self.lib.spect_sensitivity(self.handle, _ptr(s), _stream_handle(stream)))
+        return s
+
+    def info(self) -> dict:
+        sep, chunk = ctypes.c_int(), ctypes.c_int()
+        nbytes = ctypes.c_size_t()
+        _lib.check(self.lib.spect_plan_info(self.handle, ctypes.byref(sep), ctypes.byref(chunk), ctypes.byref(nbytes)))
+        return {"separable": bool(sep.value), "view_chunk": chunk.value, "device_bytes": nbytes.value}
+
+    def profile(self, enable: bool = True) -> None:
+        """Bracket every later kernel launch with CUDA events on its stream."""
+        _lib.check(self.lib.spect_profile_enable(self.handle, int(bool(enable))))
+
+    def profile_read(self, reset: bool = False) -> dict:
+        """{kernel class: (launches, summed device ms)} since the last reset."""
+        n = len(_lib.KERNEL_CLASSES)
+        la = (ctypes.c_longlong * n)()
+        ms = (ctypes.c_double * n)()
+        _lib.check(self.lib.spect_profile_read(self.handle, la, ms, int(bool(reset))))
+        return {k: (la[i], ms[i]) for i, k in enumerate(_lib.KERNEL_CLASSES)}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _lib.check(self.lib.spect_plan_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

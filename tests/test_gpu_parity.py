@@ -1,0 +1,151 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (written here, derived in the design notes): relative L2 2e-6 and
+per-element relative 1e-4 (denominator max(|o|, 1e-3 max|o|)) for A, A' and
+one EM step from the same FP32 iterate; FP32 adjoint mismatch 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2301_09710_gb300 import synthetic
+
+from gpu_helpers import (ADJ_FP32, assert_close, dev, host, make_plan, need_gpu, oracle_psf, torch)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+# ---------------------------------------------------------------- config-1 workload, full size
+@pytest.mark.parametrize("separable", [True, False])
+def test_config1_forward_back_em(separable):
+    prob = synthetic.config1(seed=0)
+    ang = oracle.default_angles(prob.nview)
+    psf = oracle_psf(prob, separable)
+    plan = make_plan(prob, ang, separable)
+    assert plan.info()["separable"] == separable
+    x = dev(prob.x)
+    v = plan.forward(x)
+    v_o = oracle.forward(prob.x, prob.mu, psf, prob.dy, ang)
+    assert_close(host(v), v_o, what="A x")
+    xb = plan.back(v)
+    xb_o = oracle.back(v_o.astype(np.float32), prob.mu, psf, prob.dy, ang)
+    assert_close(host(xb), xb_o, what="A' v")
+    # one EM step from the same FP32 iterate
+    y = synthetic.poisson_counts(v_o, 0)
+    rbar = (0.1 * v_o.mean() * np.ones_like(v_o)).astype(np.float32)
+    x0 = np.where(prob.body, 1.0, 0.0).astype(np.float32) + 0.05
+    xg = dev(x0)
+    plan.em_step(xg, dev(y), dev(rbar), niter=1)
+    x1_o = oracle.em_step(x0, y, rbar, prob.mu, psf, prob.dy, ang)
+    assert_close(host(xg), x1_o, what="EM step")
+    # FP32 adjointness through the library
+    rng = np.random.default_rng(1)
+    yy = rng.uniform(0, 1, plan.proj_shape).astype(np.float32)
+    lhs = np.vdot(host(plan.forward(x)), yy.astype(np.float64))
+    rhs = np.vdot(prob.x.astype(np.float64), host(plan.back(dev(yy))))
+    assert abs(lhs - rhs) <= ADJ_FP32 * abs(lhs)
+    plan.close()
+
+
+# ---------------------------------------------------------------- ragged and degenerate shapes
+CASES = [
+    # nx, nz, nview, px, pz, nview_psf, seed
+    (37, 13, 9, 5, 9, 9, 1),     # odd, ragged tiles, view-dependent PSF, pz wider than half nz
+    (33, 1, 4, 7, 3, 1, 2),      # nz = 1: both k-edges fold on one row
+    (2, 3, 3, 3, 5, 1, 3),       # smallest image
+    (20, 40, 1, 1, 1, 1, 4),     # delta PSF, one view
+    (48, 35, 7, 15, 11, 7, 5),   # PSF wider than tiles' halo multiple
+]
+
+
+@pytest.mark.parametrize("separable", [True, False])
+@pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}x{c[1]}v{c[2]}p{c[3]}x{c[4]}" for c in CASES])
+def test_ragged_forward_back(case, separable):
+    nx, nz, nview, px, pz, nvp, seed = case
+    prob = synthetic.random_problem(seed, nx=nx, nz=nz, nview=nview, px=px, pz=pz, nview_psf=nvp, mu_scale=0.1)
+    rng = np.random.default_rng(seed)
+    ang = rng.uniform(0, 2 * np.pi, nview)
+    ang[0] = np.pi / 2  # always include an exact quarter turn
+    psf = oracle_psf(prob, separable)
+    plan = make_plan(prob, ang, separable)
+    v = plan.forward(dev(prob.x))
+    v_o = oracle.forward(prob.x, prob.mu, psf, prob.dy, ang)
+    assert_close(host(v), v_o, what="A x")
+    yy = rng.uniform(0, 1, plan.proj_shape).astype(np.float32)
+    xb = plan.back(dev(yy))
+    xb_o = oracle.back(yy, prob.mu, psf, prob.dy, ang)
+    assert_close(host(xb), xb_o, what="A' y")
+    plan.close()
+
+
+def test_no_attenuation_map():
+    prob = synthetic.random_problem(6, nx=24, nz=8, nview=5, px=5, pz=5)
+    ang = oracle.default_angles(5)
+    from paper_2301_09710_gb300 import SpectPlan
+    plan = SpectPlan(24, 8, 5, mu=None, dy=1.0, fx=prob.fx, fz=prob.fz, angles=ang)
+    v = plan.forward(dev(prob.x))
+    v_o = oracle.forward(prob.x, np.zeros_like(prob.x), oracle.psf_from_factors(prob.fx, prob.fz), 1.0, ang)
+    assert_close(host(v), v_o, what="A x, mu = 0")
+
+
+def test_quarter_turns_exact_line_sums():
+    # mu = 0, delta PSF, views at multiples of 90 degrees: rotated line sums
+    n, nz = 16, 5
+    rng = np.random.default_rng(7)
+    x = rng.integers(0, 8, (nz, n, n)).astype(np.float32)  # small integers: sums are exact in FP32
+    from paper_2301_09710_gb300 import SpectPlan
+    fx = np.zeros((1, n, 1), np.float32) + 1
+    plan = SpectPlan(n, nz, 4, mu=None, dy=1.0, fx=fx, fz=fx.copy(), angles=np.arange(4) * np.pi / 2)
+    v = host(plan.forward(dev(x)))
+    for q in range(4):
+        want = np.stack([np.rot90(x[k], -q).sum(axis=0) for k in range(nz)])
+        np.testing.assert_array_equal(v[q], want)
+
+
+# ---------------------------------------------------------------- the paper's adjoint experiment
+@pytest.mark.parametrize("separable", [True, False])
+def test_dense_adjoint_paper_shape_fp32(separable):
+    prob = synthetic.random_problem(100, nx=8, nz=6, nview=7, px=3, pz=3, symmetric=True, mu_scale=0.3)
+    ang = oracle.default_angles(7)
+    plan = make_plan(prob, ang, separable)
+    N, M = 8 * 8 * 6, 8 * 6 * 7
+    eye_n = torch.eye(N, device="cuda", dtype=torch.float32)
+    eye_m = torch.eye(M, device="cuda", dtype=torch.float32)
+    A = np.stack([host(plan.forward(eye_n[c].reshape(plan.vol_shape))).ravel() for c in range(N)], axis=1)
+    B = np.stack([host(plan.back(eye_m[r].reshape(plan.proj_shape))).ravel() for r in range(M)], axis=1)
+    assert A.shape == (336, 384)
+    err = np.linalg.norm(A.T - B) / np.linalg.norm(A)
+    assert err < 1e-6, err  # the paper's FP32 figure (Section III-A)
+    # and the dense matrix itself against the oracle's
+    psf = oracle_psf(prob, separable)
+    A_o = np.stack([oracle.forward(e.reshape(6, 8, 8), prob.mu, psf, 1.0, ang, nthreads=1).ravel()
+                    for e in np.eye(N)], axis=1)
+    assert np.linalg.norm(A - A_o) / np.linalg.norm(A_o) < 2e-6
+
+
+# ---------------------------------------------------------------- determinism
+def test_bitwise_deterministic():
+    prob = synthetic.config1(seed=2, nx=32, nz=16, nview=16)
+    ang = oracle.default_angles(16)
+    plan = make_plan(prob, ang, True)
+    x = dev(prob.x)
+    a = host(plan.forward(x))
+    b = host(plan.forward(x))
+    np.testing.assert_array_equal(a, b)
+    c = host(plan.back(dev(a)))
+    d = host(plan.back(dev(a)))
+    np.testing.assert_array_equal(c, d)
+
+
+def test_sensitivity_matches_oracle():
+    prob = synthetic.config1(seed=3, nx=32, nz=12, nview=10, psf_size=7)
+    ang = oracle.default_angles(10)
+    plan = make_plan(prob, ang, True)
+    s = host(plan.sensitivity())
+    s_o = oracle.sensitivity(prob.mu, oracle_psf(prob, True), prob.dy, ang)
+    assert_close(s, s_o, what="A'1")
