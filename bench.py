@@ -202,7 +202,10 @@ def run_ours(args):
     prof = plan.profile_read(reset=True)
     plan.profile(False)
     pk = peaks(torch, local)
-    chunk = plan.info()["view_chunk"]
+    from paper_2301_09710_gb300.projector import fp32_peak
+    probe = fp32_peak()
+    info = plan.info()
+    chunk = info["view_chunk"]
     kern = {}
     for k, (n, ms) in prof.items():
         if n == 0:
@@ -219,6 +222,7 @@ def run_ours(args):
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
                 "frac": (achieved / pk["fp32_tflops"]) if achieved else None, "traffic": None,
                 "peak_basis": f"{pk['sms']} SMs x 128 FP32 lanes x 2 FLOP x {pk['sm_max_mhz']:.0f} MHz (max SM clock)",
+                "probe_tflops": probe,
                 "kernels": kern}
 
     # end to end through the public API: host (pinned) buffers, copies inside the timed region
@@ -278,7 +282,7 @@ def run_ours(args):
                "config": {"workload": "128x128x80 image, 128 views over 360 deg, 37x37 depth-dependent "
                                       "anisotropic Gaussian PSF (separable factors), MLEM step with 10% smoothed "
                                       "background, XCAT-like ellipsoid phantom (seed 0)",
-                          "path": args.path, "view_chunk": chunk, "parallelism": f"replicas{world}",
+                          "path": args.path, "fused": info["fused"], "view_chunk": chunk, "parallelism": f"replicas{world}",
                           "l2": "flushed between timed steps (256 MB write)",
                           "step": "one EM iteration = one A + one A' + fused ratio/update"},
                "clocks": clk.summary(), "gpu_launches": n_launch, "e2e": e2e, "roofline": roofline,

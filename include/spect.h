@@ -77,7 +77,12 @@ enum {
     SPECT_PLAN_DEFAULT = 0u,
     /* Use the separable factors when both a full PSF and factors are given
      * (otherwise the full PSF wins).  Ignored when only one form is given. */
-    SPECT_PLAN_PREFER_SEPARABLE = 1u << 0
+    SPECT_PLAN_PREFER_SEPARABLE = 1u << 0,
+    /* Keep device memory O(image + projections): recompute the attenuation
+     * per view and stream views through a small work slab, instead of
+     * caching the attenuation factors of every view (nview * nx*ny*nz floats)
+     * and using the fused kernels. */
+    SPECT_PLAN_LOW_MEMORY = 1u << 1
 };
 
 /*
@@ -157,11 +162,23 @@ spect_status spect_sensitivity(spect_plan plan, float* s, spect_stream stream);
 
 /*
  * spect_plan_info -- describe a plan (host out-pointers; any may be NULL):
- *   separable   1 when the separable-factor kernels are used, else 0.
- *   view_chunk  views processed per pass through the work slab.
+ *   separable    1 when the separable-factor kernels are used, else 0.
+ *   fused        1 when the fused kernels with the cached attenuation serve
+ *                the plan, 0 for the low-memory kernels.
+ *   view_chunk   views processed per pass through the work slab.
  *   device_bytes device memory held by the plan (state + work slab).
  */
-spect_status spect_plan_info(spect_plan plan, int* separable, int* view_chunk, size_t* device_bytes);
+spect_status spect_plan_info(spect_plan plan, int* separable, int* fused, int* view_chunk, size_t* device_bytes);
+
+/*
+ * spect_fp32_peak -- measure the FP32 fused multiply-add throughput of the
+ * current device with a register-resident dependent-chain kernel (no memory
+ * traffic): tflops_ffma for scalar fmaf, tflops_ffma2 for the packed
+ * two-lane form (__ffma2_rn); FLOP = 2 per lane FMA.  Host out-pointers;
+ * synchronises `stream`.  A measurement aid for roofline reporting (the
+ * paper has no counterpart).
+ */
+spect_status spect_fp32_peak(double* tflops_ffma, double* tflops_ffma2, spect_stream stream);
 
 /* Kernel classes for spect_profile_read(). */
 enum {

@@ -20,6 +20,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "spect.h")
 STATUS = {0: "SPECT_OK", 1: "SPECT_EINVAL", 2: "SPECT_ENOMEM", 3: "SPECT_ECUDA", 4: "SPECT_ETIMEOUT",
           5: "SPECT_EUNSUPPORTED"}
 SPECT_PLAN_PREFER_SEPARABLE = 1
+SPECT_PLAN_LOW_MEMORY = 2
 KERNEL_CLASSES = ["rotate_atten", "conv_fwd", "conv_adj", "rotate_adj", "other"]
 
 
@@ -65,12 +66,15 @@ def load(path: str = LIB_PATH):
         lib.spect_em_step.restype = st
         lib.spect_sensitivity.argtypes = [vp, vp, vp]
         lib.spect_sensitivity.restype = st
-        lib.spect_plan_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_size_t)]
+        lib.spect_plan_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                                        ctypes.POINTER(ctypes.c_size_t)]
         lib.spect_plan_info.restype = st
         lib.spect_profile_enable.argtypes = [vp, i]
         lib.spect_profile_enable.restype = st
         lib.spect_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double), i]
         lib.spect_profile_read.restype = st
+        lib.spect_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
+        lib.spect_fp32_peak.restype = st
         lib.spect_plan_destroy.argtypes = [vp]
         lib.spect_plan_destroy.restype = st
         lib.spect_last_error.argtypes = []

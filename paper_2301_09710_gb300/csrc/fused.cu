@@ -1,0 +1,666 @@
+// fused.cu -- the default (fast) path of the projector on sm_103a.
+//
+// Same operator as the kernels in rotate.cu / conv.cu (Section II-A of
+// arXiv 2301.09710, Algorithms 1 and 2), organised for GB300:
+//
+//  * Internal volumes use a k-fastest layout [j][i][k] ("transposed"): the
+//    bilinear rotation weights depend on (i, j, view) only, so each of the four
+//    neighbours of a rotated sample is a contiguous run of nz floats and every
+//    rotation gather is a coalesced 128-byte access with lanes over k.
+//  * The Eq. (1) attenuation factor mubar is computed once per plan for every
+//    view, [l][j][i][k] (nview * nx*ny*nz floats; HBM is plentiful), so the hot
+//    kernels multiply by a streamed, coalesced value instead of re-rotating mu.
+//  * Forward: one block per (view, group of J depth planes).  Per plane it
+//    rotates and attenuates the whole (i,k) plane into shared memory, runs the
+//    separable PSF blur as two register-blocked sliding-window passes (i, then
+//    k, replicate padding materialised as halo rows/columns), and accumulates
+//    the plane into register partial sums; the groups' partials are added in
+//    a fixed order by a small reduce kernel (deterministic, no atomics).
+//  * Transpose: one block per (view, depth group) expands the detector plane
+//    into blurred-adjoint planes times mubar (the t slab, [v][j][i][k]); a
+//    gather kernel then sums sum_l sum_p W_l(p;q) t_l(p,k) per destination voxel
+//    q over fixed-length adjacency lists (weights bitwise those of A).
+#include "spect_internal.cuh"
+
+namespace spect {
+
+namespace {
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Rotation table entry of rotated-frame pixel (i, j): base voxel index
+// (i0c + nx*j0c, clamped so all four reads are in bounds) and the four weights
+// of slots (0,0), (1,0), (0,1), (1,1) relative to it; neighbours outside the
+// slice (zero padding) get weight 0.
+__device__ __forceinline__ void rot_table_entry(int i, int j, const ViewRot r, const Geometry& g, float4& w, int& base)
+{
+    const Sample s = rot_sample(i, j, r, g.cint, g.cfrac);
+    const int bi = clampi(s.i0, 0, g.nx - 2), bj = clampi(s.j0, 0, g.ny - 2);
+    float ww[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+        for (int di = 0; di < 2; ++di) {
+            const int qi = s.i0 + di, qj = s.j0 + dj;
+            if (qi >= 0 && qi < g.nx && qj >= 0 && qj < g.ny) ww[(qi - bi) + 2 * (qj - bj)] = bilinear_w(s, di, dj);
+        }
+    w = make_float4(ww[0], ww[1], ww[2], ww[3]);
+    base = bi + g.nx * bj;
+}
+
+}  // namespace
+
+// ============================================================================
+// Plan-time kernels
+// ============================================================================
+
+// out[c][r] = in[r][c] for an R x C matrix (tiled through shared memory).
+__global__ void k_transpose(const float* __restrict__ in, float* __restrict__ out, int R, int C)
+{
+    __shared__ float tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+        const int r = r0 + dy, c = c0 + threadIdx.x;
+        if (r < R && c < C) tile[dy][threadIdx.x] = in[(size_t)r * C + c];
+    }
+    __syncthreads();
+    for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+        const int c = c0 + dy, r = r0 + threadIdx.x;
+        if (r < R && c < C) out[(size_t)c * R + r] = tile[threadIdx.x][dy];
+    }
+}
+
+cudaError_t launch_transpose(const float* in, float* out, int R, int C, cudaStream_t st)
+{
+    dim3 grid((C + 31) / 32, (R + 31) / 32);
+    k_transpose<<<grid, dim3(32, 8), 0, st>>>(in, out, R, C);
+    return cudaGetLastError();
+}
+
+// mubar[l][j][i][k] = exp(-dy (mu~(j)/2 + sum_{s>j} mu~(s))), Eq. (1), for every
+// view; one thread per (l, i, k) walking j from the detector side.  mu_t is mu
+// in the [j][i][k] layout.
+__global__ void k_mubar_cache(Geometry g, const ViewRot* __restrict__ rot, const float* __restrict__ mu_t,
+                              float* __restrict__ mubar)
+{
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t per_view = (size_t)g.nx * g.nz;
+    if (idx >= per_view * g.nview) return;
+    const int l = (int)(idx / per_view);
+    const int rem = (int)(idx - (size_t)l * per_view);
+    const int i = rem / g.nz, k = rem - i * g.nz;
+    const ViewRot r = rot[l];
+    AttenScan sc;
+    for (int j = g.ny - 1; j >= 0; --j) {
+        float4 w;
+        int base;
+        rot_table_entry(i, j, r, g, w, base);
+        const float* m = mu_t + (size_t)base * g.nz + k;
+        const size_t rs = (size_t)g.nx * g.nz;
+        float mv = 0.f;
+        mv = __fmaf_rn(w.x, m[0], mv);
+        mv = __fmaf_rn(w.y, m[g.nz], mv);
+        mv = __fmaf_rn(w.z, m[rs], mv);
+        mv = __fmaf_rn(w.w, m[rs + g.nz], mv);
+        mubar[(((size_t)l * g.ny + j) * g.nx + i) * g.nz + k] = g.has_mu ? sc.step(mv, g.dy) : 1.f;
+    }
+}
+
+cudaError_t launch_mubar_cache(const spect_plan_s& P, const float* mu_t, cudaStream_t st)
+{
+    const size_t n = (size_t)P.g.nx * P.g.nz * P.g.nview;
+    k_mubar_cache<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.g, P.rot, mu_t, P.mubar);
+    return cudaGetLastError();
+}
+
+// Fixed-length adjacency lists for the transposed rotation: for destination
+// q and view l, up to `maxe` (source pixel p, weight) pairs, zero-padded.  The
+// candidate search and weights are those of k_build_adjacency (rotate.cu).
+__global__ void k_build_adjacency_fixed(Geometry g, const ViewRot* __restrict__ rot, int maxe, AdjEntry* adj)
+{
+    const size_t nxy = (size_t)g.nx * g.ny;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nxy * g.nview) return;
+    const int l = (int)(idx / nxy);
+    const int q = (int)(idx % nxy);
+    const int qi = q % g.nx, qj = q / g.nx;
+    const ViewRot r = rot[l];
+    const float ct = r.ct_hi + r.ct_lo, st = r.st_hi + r.st_lo;
+    const float c = (float)g.cint + g.cfrac;
+    const float dqi = (float)qi - c, dqj = (float)qj - c;
+    const float pi_ = c + ct * dqi - st * dqj;
+    const float pj_ = c + st * dqi + ct * dqj;
+    const int bi = (int)floorf(pi_) - 1, bj = (int)floorf(pj_) - 1;
+    AdjEntry* out = adj + idx * maxe;
+    int cnt = 0;
+    for (int cj = 0; cj < 4; ++cj)
+        for (int ci = 0; ci < 4; ++ci) {
+            const int pi = bi + ci, pj = bj + cj;
+            if (pi < 0 || pi >= g.nx || pj < 0 || pj >= g.ny) continue;
+            const Sample s = rot_sample(pi, pj, r, g.cint, g.cfrac);
+            const int di = qi - s.i0, dj = qj - s.j0;
+            if (di < 0 || di > 1 || dj < 0 || dj > 1) continue;
+            const float w = bilinear_w(s, di, dj);
+            if (w == 0.f || cnt >= maxe) continue;
+            AdjEntry e;
+            e.p = pi + g.nx * pj;
+            e.w = w;
+            out[cnt++] = e;
+        }
+    for (; cnt < maxe; ++cnt) {
+        AdjEntry e;
+        e.p = 0;
+        e.w = 0.f;
+        out[cnt] = e;
+    }
+}
+
+cudaError_t launch_build_adjacency_fixed(const spect_plan_s& P, cudaStream_t st)
+{
+    const size_t n = (size_t)P.g.nx * P.g.ny * P.g.nview;
+    k_build_adjacency_fixed<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.g, P.rot, P.adj_max, P.adjf);
+    return cudaGetLastError();
+}
+
+// ============================================================================
+// Fused forward, separable PSF, padded tap count P (odd).
+// ============================================================================
+template <int P>
+struct Sep {
+    static constexpr int C = (P - 1) / 2;    // tap centre
+    static constexpr int CX = 8;             // i outputs per thread (i-pass)
+    static constexpr int CZ = 8;             // k outputs per thread (k-pass)
+    static constexpr int ZH = (C + 3) & ~3;  // k halo columns, 16-byte aligned
+    static constexpr int WZ = CZ + 2 * ZH;   // k-pass window (multiple of 4)
+    static constexpr int PT = (P + 3) & ~3;  // tap array length
+};
+
+constexpr int kFusedThreads = 640;
+constexpr int kMaxZ = 4;  // k-pass items per thread
+
+// Shared-memory plan of a fused kernel, computed identically on host and device.
+struct FusedDims {
+    int kpw;    // W row pitch (>= nz, odd: conflict-free column stores)
+    int warea;  // floats reserved for W (multiple of 4, keeps U 16-byte aligned)
+    int kpu;    // U row pitch (>= nkb*CZ + 2*ZH, multiple of 4, pitch/4 odd)
+    int wrows;  // W rows: nib*CX + 2*C
+    int nib, nkb;
+    int J, G;   // depth planes per block, depth groups
+};
+
+__host__ __device__ inline size_t fused_smem_floats(const FusedDims& d, int nx, int PT)
+{
+    return (size_t)d.warea + (size_t)nx * d.kpu + 6 * (size_t)PT + 5 * (size_t)nx;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, FusedDims d,
+                                                                     const ViewRot* __restrict__ rot,
+                                                                     const float* __restrict__ xt,
+                                                                     const float* __restrict__ mubar,
+                                                                     const float* __restrict__ fx,
+                                                                     const float* __restrict__ fz,
+                                                                     float* __restrict__ part, int l0)
+{
+    using S = Sep<P>;
+    constexpr int C = S::C, CX = S::CX, CZ = S::CZ, ZH = S::ZH, WZ = S::WZ, PT = S::PT;
+    extern __shared__ __align__(16) float sm[];
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    float* W = sm;                                   // wrows x kpw, row C+i holds plane row i
+    float* U = W + d.warea;                          // nx x kpu, column ZH+k holds k
+    float* FX = U + (size_t)nx * d.kpu;              // PT taps
+    float* FZ = FX + PT;
+    float4* TW = reinterpret_cast<float4*>(FZ + PT);  // nx weights (16-byte aligned: offsets are multiples of 4)
+    int* TB = reinterpret_cast<int*>(TW + nx);        // nx bases
+    const int tid = threadIdx.x;
+    const int T = kFusedThreads;
+    const int grp = blockIdx.x, l = l0 + blockIdx.y;
+    const int lp = g.nvp == 1 ? 0 : l;
+    const int j_begin = grp * d.J, j_end = min(ny, j_begin + d.J);
+    const ViewRot r = rot[l];
+    const int ox = (P - g.px) / 2, oz = (P - g.pz) / 2;  // zero-padding offsets of the taps
+    const size_t pln = (size_t)nx * nz;
+
+    float acc[kMaxZ][CZ];
+#pragma unroll
+    for (int q = 0; q < kMaxZ; ++q)
+#pragma unroll
+        for (int c = 0; c < CZ; ++c) acc[q][c] = 0.f;
+
+    for (int j = j_begin; j < j_end; ++j) {
+        // taps (zero-padded to P, centred) and the rotation table of row j
+        for (int a = tid; a < PT; a += T) {
+            const int ax = a - ox, az = a - oz;
+            FX[a] = (ax >= 0 && ax < g.px) ? fx[((size_t)lp * ny + j) * g.px + ax] : 0.f;
+            FZ[a] = (az >= 0 && az < g.pz) ? fz[((size_t)lp * ny + j) * g.pz + az] : 0.f;
+        }
+        for (int i = tid; i < nx; i += T) rot_table_entry(i, j, r, g, TW[i], TB[i]);
+        __syncthreads();
+
+        // rotate + attenuate the (i,k) plane into W (rows C..C+nx-1), replicate halo rows
+        const float* mb = mubar + ((size_t)l * ny + j) * pln;
+        for (int f = tid; f < nx * nz; f += T) {
+            const int i = f / nz, k = f - i * nz;
+            const float4 w = TW[i];
+            const float* xb = xt + (size_t)TB[i] * nz + k;
+            float v = w.x * __ldg(xb);
+            v = fmaf(w.y, __ldg(xb + nz), v);
+            v = fmaf(w.z, __ldg(xb + pln), v);
+            v = fmaf(w.w, __ldg(xb + pln + nz), v);
+            v *= __ldg(mb + f);
+            W[(C + i) * d.kpw + k] = v;
+            if (i == 0)
+                for (int h = 0; h < C; ++h) W[h * d.kpw + k] = v;
+            if (i == nx - 1)
+                for (int h = C + nx; h < d.wrows; ++h) W[h * d.kpw + k] = v;
+        }
+        __syncthreads();
+
+        // i-pass: U(i,k) = sum_a fx(a) w(clamp(i-a+cx), k); lanes over k
+        for (int it = tid; it < nz * d.nib; it += T) {
+            const int ib = it / nz, k = it - ib * nz;
+            const int i0 = ib * CX;
+            float win[CX + P - 1];
+#pragma unroll
+            for (int m = 0; m < CX + P - 1; ++m) win[m] = W[(i0 + m) * d.kpw + k];
+            float o[CX];
+#pragma unroll
+            for (int c = 0; c < CX; ++c) o[c] = 0.f;
+#pragma unroll
+            for (int a4 = 0; a4 < PT / 4; ++a4) {
+                const float4 f4 = reinterpret_cast<const float4*>(FX)[a4];
+                const float fv[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int a = 4 * a4 + u;
+                    if (a < P) {
+#pragma unroll
+                        for (int c = 0; c < CX; ++c) o[c] = fmaf(fv[u], win[c - a + P - 1], o[c]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CX; ++c) {
+                const int i = i0 + c;
+                if (i < nx) {
+                    float* ur = U + (size_t)i * d.kpu;
+                    ur[ZH + k] = o[c];
+                    if (k == 0)
+                        for (int h = 0; h < ZH; ++h) ur[h] = o[c];
+                    if (k == nz - 1)
+                        for (int h = ZH + nz; h < d.kpu; ++h) ur[h] = o[c];
+                }
+            }
+        }
+        __syncthreads();
+
+        // k-pass into the register partial sums: lanes over i
+#pragma unroll
+        for (int q = 0; q < kMaxZ; ++q) {
+            const int it = tid + q * T;
+            if (it < nx * d.nkb) {
+                const int kb = it / nx, i = it - kb * nx;
+                const float4* row = reinterpret_cast<const float4*>(U + (size_t)i * d.kpu + kb * CZ);
+                float win[WZ];
+#pragma unroll
+                for (int m4 = 0; m4 < WZ / 4; ++m4) {
+                    const float4 t = row[m4];
+                    win[4 * m4] = t.x;
+                    win[4 * m4 + 1] = t.y;
+                    win[4 * m4 + 2] = t.z;
+                    win[4 * m4 + 3] = t.w;
+                }
+                float o[CZ];
+#pragma unroll
+                for (int c = 0; c < CZ; ++c) o[c] = 0.f;
+#pragma unroll
+                for (int b4 = 0; b4 < PT / 4; ++b4) {
+                    const float4 f4 = reinterpret_cast<const float4*>(FZ)[b4];
+                    const float fv[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int b = 4 * b4 + u;
+                        if (b < P) {
+#pragma unroll
+                            for (int c = 0; c < CZ; ++c) o[c] = fmaf(fv[u], win[c - b + C + ZH], o[c]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < CZ; ++c) acc[q][c] += o[c];
+            }
+        }
+        __syncthreads();
+    }
+
+    // partial depth sums of this group: part[grp][l][k][i]
+#pragma unroll
+    for (int q = 0; q < kMaxZ; ++q) {
+        const int it = tid + q * T;
+        if (it < nx * d.nkb) {
+            const int kb = it / nx, i = it - kb * nx;
+#pragma unroll
+            for (int c = 0; c < CZ; ++c) {
+                const int k = kb * CZ + c;
+                if (k < nz) part[(((size_t)grp * g.nview + l) * nz + k) * nx + i] = acc[q][c];
+            }
+        }
+    }
+}
+
+// v(i,k,l) = sum over depth groups of the partials (fixed order), optionally
+// turned into the EM ratio y / (v + rbar).
+__global__ void k_fwd_reduce(const float* __restrict__ part, int G, size_t nproj, float* __restrict__ v,
+                             const float* __restrict__ em_y, const float* __restrict__ em_rbar)
+{
+    const size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= nproj) return;
+    float s = 0.f;
+    for (int gq = 0; gq < G; ++gq) s += part[(size_t)gq * nproj + o];
+    if (em_y) {
+        const float yb = s + (em_rbar ? em_rbar[o] : 0.f);
+        v[o] = yb > 0.f ? em_y[o] / yb : 0.f;
+    } else {
+        v[o] = s;
+    }
+}
+
+// ============================================================================
+// Fused transpose of the blur + attenuation, separable PSF.
+// ============================================================================
+template <int P>
+__global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, FusedDims d, int cls_z,
+                                                                     const float* __restrict__ vin,
+                                                                     const float* __restrict__ mubar,
+                                                                     const float* __restrict__ fx_adj,
+                                                                     const float* __restrict__ fz_adj,
+                                                                     float* __restrict__ slab, int l0)
+{
+    using S = Sep<P>;
+    constexpr int C = S::C, CX = S::CX, CZ = S::CZ, ZH = S::ZH, WZ = S::WZ, PT = S::PT;
+    extern __shared__ __align__(16) float sm[];
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    float* Zb = sm;                                 // wrows x kpw: row C+i = k-adjoint of row i, zero halo rows
+    float* V = Zb + d.warea;                        // nx x kpu: detector plane, column ZH+k, zero halo
+    float* FX = V + (size_t)nx * d.kpu;             // 3 classes x PT
+    float* FZ = FX + 3 * PT;                        // 3 classes x PT
+    const int tid = threadIdx.x;
+    const int T = kFusedThreads;
+    const int grp = blockIdx.x, v = blockIdx.y, l = l0 + v;
+    const int lp = g.nvp == 1 ? 0 : l;
+    const int j_begin = grp * d.J, j_end = min(ny, j_begin + d.J);
+    const int ox = (P - g.px) / 2, oz = (P - g.pz) / 2;
+    const size_t nrow = (size_t)g.nvp * ny;
+    const size_t pln = (size_t)nx * nz;
+
+    // stage the detector plane v(:,:,l) transposed, zero outside the detector
+    for (int e = tid; e < nx * d.kpu; e += T) V[e] = 0.f;
+    for (int e = tid; e < d.wrows * d.kpw; e += T) Zb[e] = 0.f;
+    __syncthreads();
+    for (int e = tid; e < nx * nz; e += T) {
+        const int k = e / nx, i = e - k * nx;
+        V[(size_t)i * d.kpu + ZH + k] = vin[((size_t)l * nz + k) * nx + i];
+    }
+
+    for (int j = j_begin; j < j_end; ++j) {
+        for (int e = tid; e < 3 * PT; e += T) {
+            const int c = e / PT, a = e - c * PT;
+            const int ax = a - ox, az = a - oz;
+            FX[e] = (ax >= 0 && ax < g.px) ? fx_adj[((size_t)c * nrow + (size_t)lp * ny + j) * g.px + ax] : 0.f;
+            FZ[e] = (c < cls_z && az >= 0 && az < g.pz) ? fz_adj[((size_t)c * nrow + (size_t)lp * ny + j) * g.pz + az]
+                                                       : 0.f;
+        }
+        __syncthreads();
+
+        // k-adjoint: Zb(C+i, k) = sum_b' fz~(b') v(i, k+b'-cz), lanes over i
+        for (int it = tid; it < nx * d.nkb; it += T) {
+            const int kb = it / nx, i = it - kb * nx;
+            const float4* row = reinterpret_cast<const float4*>(V + (size_t)i * d.kpu + kb * CZ);
+            float win[WZ];
+#pragma unroll
+            for (int m4 = 0; m4 < WZ / 4; ++m4) {
+                const float4 t = row[m4];
+                win[4 * m4] = t.x;
+                win[4 * m4 + 1] = t.y;
+                win[4 * m4 + 2] = t.z;
+                win[4 * m4 + 3] = t.w;
+            }
+            float o[CZ];
+#pragma unroll
+            for (int c = 0; c < CZ; ++c) o[c] = 0.f;
+#pragma unroll
+            for (int b4 = 0; b4 < PT / 4; ++b4) {
+                const float4 f4 = reinterpret_cast<const float4*>(FZ)[b4];
+                const float fv[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int b = 4 * b4 + u;
+                    if (b < P) {
+#pragma unroll
+                        for (int c = 0; c < CZ; ++c) o[c] = fmaf(fv[u], win[c + b - C + ZH], o[c]);
+                    }
+                }
+            }
+            const int k0 = kb * CZ;
+            if (nz > 1) {  // replicate-padding folds on the first and last detector rows
+#pragma unroll
+                for (int c = 0; c < CZ; ++c) {
+                    const int k = k0 + c;
+                    if (k == 0 || k == nz - 1) {
+                        const float* f = FZ + (k == 0 ? 1 : 2) * PT;
+                        float s = 0.f;
+#pragma unroll
+                        for (int b = 0; b < P; ++b) s = fmaf(f[b], win[c + b - C + ZH], s);
+                        o[c] = s;
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CZ; ++c)
+                if (k0 + c < nz) Zb[(size_t)(C + i) * d.kpw + k0 + c] = o[c];
+        }
+        __syncthreads();
+
+        // i-adjoint times mubar -> t slab [v][j][i][k]; lanes over k
+        const float* mb = mubar + ((size_t)l * ny + j) * pln;
+        float* tout = slab + ((size_t)v * ny + j) * pln;
+        for (int it = tid; it < nz * d.nib; it += T) {
+            const int ib = it / nz, k = it - ib * nz;
+            const int i0 = ib * CX;
+            float win[CX + P - 1];
+#pragma unroll
+            for (int m = 0; m < CX + P - 1; ++m) win[m] = Zb[(i0 + m) * d.kpw + k];
+            float o[CX];
+#pragma unroll
+            for (int c = 0; c < CX; ++c) o[c] = 0.f;
+#pragma unroll
+            for (int a4 = 0; a4 < PT / 4; ++a4) {
+                const float4 f4 = reinterpret_cast<const float4*>(FX)[a4];
+                const float fv[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int a = 4 * a4 + u;
+                    if (a < P) {
+#pragma unroll
+                        for (int c = 0; c < CX; ++c) o[c] = fmaf(fv[u], win[c + a], o[c]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CX; ++c) {
+                const int i = i0 + c;
+                if (i == 0 || i == nx - 1) {
+                    const float* f = FX + (i == 0 ? 1 : 2) * PT;
+                    float s = 0.f;
+#pragma unroll
+                    for (int a = 0; a < P; ++a) s = fmaf(f[a], win[c + a], s);
+                    o[c] = s;
+                }
+                if (i < nx) tout[(size_t)i * nz + k] = o[c] * __ldg(mb + (size_t)i * nz + k);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// x_t(q,k) (+)= sum_{v in chunk} sum_{e < maxe} w_e t[v][p_e][k]  (lanes over k)
+// with the MLEM update x <- x e / s on the last chunk when em_x is set.
+__global__ void __launch_bounds__(256) k_adj_rot_t(Geometry g, int maxe, const AdjEntry* __restrict__ adj,
+                                                   const float* __restrict__ slab, int l0, int nv, float* out,
+                                                   int accumulate, float* em_x, const float* __restrict__ em_s)
+{
+    const size_t nxy = (size_t)g.nx * g.ny;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nxy * g.nz) return;
+    const size_t q = idx / g.nz;
+    const int k = (int)(idx - q * g.nz);
+    KSum acc;
+    for (int v = 0; v < nv; ++v) {
+        const AdjEntry* e = adj + ((size_t)(l0 + v) * nxy + q) * maxe;
+        const float* t = slab + (size_t)v * nxy * g.nz + k;
+        for (int m = 0; m < maxe; ++m) {
+            const AdjEntry a = e[m];
+            acc.add(a.w * __ldg(t + (size_t)a.p * g.nz));
+        }
+    }
+    float val = acc.value();
+    if (accumulate) val += out[idx];
+    if (em_x) {
+        const float s = em_s[idx];
+        em_x[idx] = s > 0.f ? (em_x[idx] * val) / s : 0.f;
+    } else {
+        out[idx] = val;
+    }
+}
+
+// ============================================================================
+// host side: dimensioning and launchers
+// ============================================================================
+namespace {
+constexpr int kBuckets[] = {3, 5, 7, 9, 11, 13, 15, 17, 21, 25, 29, 33, 37};
+
+template <int P>
+FusedDims dims_for(const Geometry& g, int J)
+{
+    using S = Sep<P>;
+    FusedDims d;
+    d.nib = (g.nx + S::CX - 1) / S::CX;
+    d.nkb = (g.nz + S::CZ - 1) / S::CZ;
+    d.wrows = d.nib * S::CX + 2 * S::C;
+    d.kpw = g.nz | 1;
+    d.warea = (d.wrows * d.kpw + 3) & ~3;
+    int kpu = d.nkb * S::CZ + 2 * S::ZH;
+    kpu = (kpu + 3) & ~3;
+    if (((kpu / 4) & 1) == 0) kpu += 4;
+    d.kpu = kpu;
+    d.J = J;
+    d.G = (g.ny + J - 1) / J;
+    return d;
+}
+
+template <int P>
+size_t smem_for(const Geometry& g, const FusedDims& d)
+{
+    return fused_smem_floats(d, g.nx, Sep<P>::PT) * sizeof(float);
+}
+
+template <int P>
+bool fits(const Geometry& g, size_t limit)
+{
+    const FusedDims d = dims_for<P>(g, 8);
+    return smem_for<P>(g, d) <= limit && (size_t)g.nx * d.nkb <= (size_t)kFusedThreads * kMaxZ;
+}
+
+template <int P>
+cudaError_t fwd_launch(const spect_plan_s& Pl, const float* xt, int l0, int nv, cudaStream_t st)
+{
+    const FusedDims d = dims_for<P>(Pl.g, Pl.fused_J);
+    const size_t smem = smem_for<P>(Pl.g, d);
+    cudaError_t e = cudaFuncSetAttribute(k_fwd_sep_fused<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_fwd_sep_fused<P><<<dim3(d.G, nv), kFusedThreads, smem, st>>>(Pl.g, d, Pl.rot, xt, Pl.mubar, Pl.fx, Pl.fz,
+                                                                    Pl.part, l0);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t adj_launch(const spect_plan_s& Pl, const float* v, int l0, int nv, cudaStream_t st)
+{
+    const FusedDims d = dims_for<P>(Pl.g, Pl.fused_J);
+    const size_t smem = smem_for<P>(Pl.g, d);
+    cudaError_t e = cudaFuncSetAttribute(k_adj_sep_fused<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_adj_sep_fused<P><<<dim3(d.G, nv), kFusedThreads, smem, st>>>(Pl.g, d, Pl.cls_z, v, Pl.mubar, Pl.fx_adj,
+                                                                    Pl.fz_adj, Pl.slab, l0);
+    return cudaGetLastError();
+}
+}  // namespace
+
+int fused_bucket(const Geometry& g, size_t smem_limit)
+{
+    const int p = g.px > g.pz ? g.px : g.pz;
+    for (int b : kBuckets) {
+        if (b < p) continue;
+        bool ok = false;
+        switch (b) {
+#define SPECT_FITS(B) \
+    case B: ok = fits<B>(g, smem_limit); break;
+            SPECT_FITS(3) SPECT_FITS(5) SPECT_FITS(7) SPECT_FITS(9) SPECT_FITS(11) SPECT_FITS(13) SPECT_FITS(15)
+            SPECT_FITS(17) SPECT_FITS(21) SPECT_FITS(25) SPECT_FITS(29) SPECT_FITS(33) SPECT_FITS(37)
+#undef SPECT_FITS
+            default: break;
+        }
+        return ok ? b : 0;
+    }
+    return 0;
+}
+
+int fused_groups(const spect_plan_s& P) { return (P.g.ny + P.fused_J - 1) / P.fused_J; }
+
+#define SPECT_DISPATCH(FN, ...)                        \
+    switch (P.bucket) {                                \
+        case 3: return FN<3>(__VA_ARGS__);             \
+        case 5: return FN<5>(__VA_ARGS__);             \
+        case 7: return FN<7>(__VA_ARGS__);             \
+        case 9: return FN<9>(__VA_ARGS__);             \
+        case 11: return FN<11>(__VA_ARGS__);           \
+        case 13: return FN<13>(__VA_ARGS__);           \
+        case 15: return FN<15>(__VA_ARGS__);           \
+        case 17: return FN<17>(__VA_ARGS__);           \
+        case 21: return FN<21>(__VA_ARGS__);           \
+        case 25: return FN<25>(__VA_ARGS__);           \
+        case 29: return FN<29>(__VA_ARGS__);           \
+        case 33: return FN<33>(__VA_ARGS__);           \
+        case 37: return FN<37>(__VA_ARGS__);           \
+        default: return cudaErrorInvalidValue;         \
+    }
+
+cudaError_t launch_fused_forward(const spect_plan_s& P, const float* xt, int l0, int nv, cudaStream_t st)
+{
+    SPECT_DISPATCH(fwd_launch, P, xt, l0, nv, st)
+}
+
+cudaError_t launch_fused_adjoint(const spect_plan_s& P, const float* v, int l0, int nv, cudaStream_t st)
+{
+    SPECT_DISPATCH(adj_launch, P, v, l0, nv, st)
+}
+#undef SPECT_DISPATCH
+
+cudaError_t launch_fwd_reduce(const spect_plan_s& P, float* v, const float* em_y, const float* em_rbar,
+                              cudaStream_t st)
+{
+    const size_t nproj = (size_t)P.g.nx * P.g.nz * P.g.nview;
+    k_fwd_reduce<<<(unsigned)((nproj + 255) / 256), 256, 0, st>>>(P.part, fused_groups(P), nproj, v, em_y, em_rbar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_rot_t(const spect_plan_s& P, int l0, int nv, float* out, int accumulate, float* em_x,
+                             const float* em_s, cudaStream_t st)
+{
+    const size_t n = (size_t)P.g.nx * P.g.ny * P.g.nz;
+    k_adj_rot_t<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.g, P.adj_max, P.adjf, P.slab, l0, nv, out, accumulate,
+                                                            em_x, em_s);
+    return cudaGetLastError();
+}
+
+}  // namespace spect

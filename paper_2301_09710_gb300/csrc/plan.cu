@@ -84,19 +84,20 @@ void free_plan(spect_plan_s* P)
         cudaEventDestroy(p.b);
     }
     for (cudaEvent_t e : P->evpool) cudaEventDestroy(e);
-    void* ptrs[] = {P->mu, P->psf, P->psf_adj, P->fx, P->fz, P->fx_adj, P->fz_adj, P->rot,
-                    P->adj_off, P->adj, P->slab, P->e, P->ratio, P->s};
+    void* ptrs[] = {P->mu, P->psf, P->psf_adj, P->fx, P->fz, P->fx_adj, P->fz_adj, P->rot, P->adj_off, P->adj,
+                    P->slab, P->e, P->ratio, P->s, P->mubar, P->xt, P->et, P->st, P->part, P->adjf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete P;
 }
 
-size_t slab_budget_bytes()
+size_t slab_budget_bytes(bool fast)
 {
-    // Work slab size: chosen so a chunk of views stays resident in L2 by
-    // default; SPECT_SLAB_MB overrides (tuning).
+    // Work slab size.  The fused path takes every view in one pass when the
+    // slab fits 1 GiB; the low-memory path keeps it at 256 MiB.
+    // SPECT_SLAB_MB overrides (tuning).
     const char* env = getenv("SPECT_SLAB_MB");
-    long mb = env ? atol(env) : 256;
+    long mb = env ? atol(env) : (fast ? 1024 : 256);
     if (mb < 1) mb = 1;
     return (size_t)mb << 20;
 }
@@ -176,14 +177,66 @@ spect_status run_back(spect_plan_s* P, const float* v, float* out, float* em_x, 
     return SPECT_OK;
 }
 
+// ---- fused path: internal volumes in the [j][i][k] layout
+spect_status to_internal(spect_plan_s* P, const float* x, float* xt, cudaStream_t st)
+{
+    const int nxy = P->g.nx * P->g.ny;
+    SPECT_CUDA_TRY(counted(P, SPECT_K_OTHER, st, [&] { return spect::launch_transpose(x, xt, P->g.nz, nxy, st); }),
+                   "transpose launch");
+    return SPECT_OK;
+}
+
+spect_status from_internal(spect_plan_s* P, const float* xt, float* x, cudaStream_t st)
+{
+    const int nxy = P->g.nx * P->g.ny;
+    SPECT_CUDA_TRY(counted(P, SPECT_K_OTHER, st, [&] { return spect::launch_transpose(xt, x, nxy, P->g.nz, st); }),
+                   "transpose launch");
+    return SPECT_OK;
+}
+
+// v = A x_t (x_t internal layout); with y set, v receives the EM ratio y / (A x + rbar)
+spect_status fast_forward(spect_plan_s* P, const float* xt, float* v, const float* y, const float* rbar,
+                          cudaStream_t st)
+{
+    SPECT_CUDA_TRY(counted(P, SPECT_K_CONV_FWD, st,
+                           [&] { return spect::launch_fused_forward(*P, xt, 0, P->g.nview, st); }),
+                   "fused forward launch");
+    SPECT_CUDA_TRY(counted(P, SPECT_K_OTHER, st, [&] { return spect::launch_fwd_reduce(*P, v, y, rbar, st); }),
+                   "depth-group reduce launch");
+    return SPECT_OK;
+}
+
+// out_t = A' v (internal layout); with em_xt set the last chunk applies x <- x out / s_t instead
+spect_status fast_back(spect_plan_s* P, const float* v, float* out_t, float* em_xt, const float* em_st,
+                       cudaStream_t st)
+{
+    const int nview = P->g.nview;
+    for (int l0 = 0; l0 < nview; l0 += P->chunk) {
+        const int nv = std::min(P->chunk, nview - l0);
+        const bool last = l0 + nv >= nview;
+        SPECT_CUDA_TRY(counted(P, SPECT_K_CONV_ADJ, st, [&] { return spect::launch_fused_adjoint(*P, v, l0, nv, st); }),
+                       "fused adjoint launch");
+        float* emx = (last && em_xt) ? em_xt : nullptr;
+        SPECT_CUDA_TRY(counted(P, SPECT_K_ROTATE_ADJ, st,
+                               [&] { return spect::launch_adj_rot_t(*P, l0, nv, out_t, l0 > 0, emx, em_st, st); }),
+                       "adjoint rotation launch");
+    }
+    return SPECT_OK;
+}
+
 spect_status ensure_sensitivity(spect_plan_s* P, cudaStream_t st)
 {
     if (P->s_valid) return SPECT_OK;
     const size_t nproj = (size_t)P->g.nx * P->g.nz * P->g.nview;
     SPECT_CUDA_TRY(counted(P, SPECT_K_OTHER, st, [&] { return spect::launch_fill(P->ratio, nproj, 1.f, st); }),
                    "fill launch");
-    spect_status r = run_back(P, P->ratio, P->s, nullptr, nullptr, st);
+    spect_status r = P->fast ? fast_back(P, P->ratio, P->st, nullptr, nullptr, st)
+                             : run_back(P, P->ratio, P->s, nullptr, nullptr, st);
     if (r != SPECT_OK) return r;
+    if (P->fast) {
+        r = from_internal(P, P->st, P->s, st);
+        if (r != SPECT_OK) return r;
+    }
     P->s_valid = 1;
     return SPECT_OK;
 }
@@ -222,7 +275,8 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
     if (!(dy >= 0.f) || !isfinite(dy)) return fail(SPECT_EINVAL, "dy must be finite and >= 0");
     if ((psf_fx == nullptr) != (psf_fz == nullptr)) return fail(SPECT_EINVAL, "give both psf_fx and psf_fz or neither");
     if (!psf && !psf_fx) return fail(SPECT_EINVAL, "no PSF given (psf or psf_fx/psf_fz)");
-    if ((flags & ~(unsigned)SPECT_PLAN_PREFER_SEPARABLE) != 0) return fail(SPECT_EINVAL, "unknown flag bits");
+    if ((flags & ~(unsigned)(SPECT_PLAN_PREFER_SEPARABLE | SPECT_PLAN_LOW_MEMORY)) != 0)
+        return fail(SPECT_EINVAL, "unknown flag bits");
     const void* ins[] = {mu, psf, psf_fx, psf_fz};
     for (const void* p : ins)
         if (p && !aligned16(p)) return fail(SPECT_EINVAL, "device inputs must be 16-byte aligned");
@@ -266,6 +320,10 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
 
     PLAN_TRY(cudaGetDevice(&dev), "cudaGetDevice");
     PLAN_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "device query");
+    if (P->separable && !(flags & SPECT_PLAN_LOW_MEMORY)) {
+        P->bucket = spect::fused_bucket(g, (size_t)smem_optin);
+        P->fast = P->bucket > 0;
+    }
     if (P->separable) {
         P->sep_tk = spect::choose_sep_tile(g, P->cls_z, (size_t)smem_optin);
         if (P->sep_tk < 1) {
@@ -349,29 +407,47 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
         PLAN_TRY(e2, "adjacency counts download");
         PLAN_TRY(e3, "adjacency max download");
         PLAN_TRY(e4, "adjacency count");
-        std::vector<int> off(nlist + 1);
-        size_t tot = 0;
-        for (size_t m = 0; m < nlist; ++m) {
-            off[m] = (int)tot;
-            tot += (size_t)counts[m];
-        }
-        off[nlist] = (int)tot;
         P->adj_max = mx;
-        PLAN_ALLOC(P->adj_off, nlist + 1, "adjacency offsets");
-        PLAN_ALLOC(P->adj, std::max<size_t>(tot, 1), "adjacency entries");
-        PLAN_TRY(cudaMemcpyAsync(P->adj_off, off.data(), (nlist + 1) * sizeof(int), cudaMemcpyHostToDevice, st),
-                 "upload adjacency offsets");
-        PLAN_TRY(spect::launch_build_adjacency(*P, 1, nullptr, nullptr, st), "adjacency fill launch");
+        if (P->fast) {
+            PLAN_ALLOC(P->adjf, nlist * (size_t)std::max(mx, 1), "adjacency lists");
+            if (mx < 1) P->adj_max = 1;
+            PLAN_TRY(spect::launch_build_adjacency_fixed(*P, st), "adjacency fill launch");
+        } else {
+            std::vector<int> off(nlist + 1);
+            size_t tot = 0;
+            for (size_t m = 0; m < nlist; ++m) {
+                off[m] = (int)tot;
+                tot += (size_t)counts[m];
+            }
+            off[nlist] = (int)tot;
+            PLAN_ALLOC(P->adj_off, nlist + 1, "adjacency offsets");
+            PLAN_ALLOC(P->adj, std::max<size_t>(tot, 1), "adjacency entries");
+            PLAN_TRY(cudaMemcpyAsync(P->adj_off, off.data(), (nlist + 1) * sizeof(int), cudaMemcpyHostToDevice, st),
+                     "upload adjacency offsets");
+            PLAN_TRY(spect::launch_build_adjacency(*P, 1, nullptr, nullptr, st), "adjacency fill launch");
+        }
         PLAN_TRY(cudaStreamSynchronize(st), "adjacency fill");
     }
 
     // work slab and EM buffers
-    const size_t budget = slab_budget_bytes();
+    const size_t budget = slab_budget_bytes(P->fast);
     P->chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)nview, budget / (vol * sizeof(float))));
     PLAN_ALLOC(P->slab, vol * (size_t)P->chunk, "work slab");
     PLAN_ALLOC(P->e, vol, "EM accumulator");
     PLAN_ALLOC(P->ratio, nproj, "EM ratio");
     PLAN_ALLOC(P->s, vol, "sensitivity");
+
+    // fused path: attenuation cache for every view, internal-layout buffers
+    if (P->fast) {
+        PLAN_ALLOC(P->mubar, vol * (size_t)nview, "attenuation cache");
+        PLAN_ALLOC(P->xt, vol, "internal image");
+        PLAN_ALLOC(P->et, vol, "internal back-projection");
+        PLAN_ALLOC(P->st, vol, "internal sensitivity");
+        PLAN_ALLOC(P->part, nproj * (size_t)spect::fused_groups(*P), "depth-group partial sums");
+        // mu in the [j][i][k] layout (temporary, the slab serves as scratch)
+        PLAN_TRY(spect::launch_transpose(P->mu, P->slab, nz, (int)nxy, st), "mu transpose launch");
+        PLAN_TRY(spect::launch_mubar_cache(*P, P->slab, st), "attenuation cache launch");
+    }
     PLAN_TRY(cudaStreamSynchronize(st), "plan set-up");
     *out = P;
     return SPECT_OK;
@@ -392,14 +468,26 @@ spect_status spect_forward(spect_plan P, const float* x, float* v, spect_stream 
 {
     spect_status r = check_call(P, x, v, "x", "v");
     if (r != SPECT_OK) return r;
-    return run_forward(P, x, v, nullptr, nullptr, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (P->fast) {
+        r = to_internal(P, x, P->xt, st);
+        if (r != SPECT_OK) return r;
+        return fast_forward(P, P->xt, v, nullptr, nullptr, st);
+    }
+    return run_forward(P, x, v, nullptr, nullptr, st);
 }
 
 spect_status spect_back(spect_plan P, const float* v, float* x, spect_stream stream)
 {
     spect_status r = check_call(P, v, x, "v", "x");
     if (r != SPECT_OK) return r;
-    return run_back(P, v, x, nullptr, nullptr, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (P->fast) {
+        r = fast_back(P, v, P->et, nullptr, nullptr, st);
+        if (r != SPECT_OK) return r;
+        return from_internal(P, P->et, x, st);
+    }
+    return run_back(P, v, x, nullptr, nullptr, st);
 }
 
 spect_status spect_sensitivity(spect_plan P, float* s, spect_stream stream)
@@ -423,6 +511,18 @@ spect_status spect_em_step(spect_plan P, float* x, const float* y, const float* 
     cudaStream_t st = (cudaStream_t)stream;
     r = ensure_sensitivity(P, st);
     if (r != SPECT_OK) return r;
+    if (P->fast) {
+        if (niter == 0) return SPECT_OK;
+        r = to_internal(P, x, P->xt, st);
+        if (r != SPECT_OK) return r;
+        for (int it = 0; it < niter; ++it) {
+            r = fast_forward(P, P->xt, P->ratio, y, rbar, st);
+            if (r != SPECT_OK) return r;
+            r = fast_back(P, P->ratio, P->et, P->xt, P->st, st);
+            if (r != SPECT_OK) return r;
+        }
+        return from_internal(P, P->xt, x, st);
+    }
     for (int it = 0; it < niter; ++it) {
         r = run_forward(P, x, P->ratio, y, rbar, st);
         if (r != SPECT_OK) return r;
@@ -455,10 +555,11 @@ spect_status spect_profile_read(spect_plan P, long long* launches, double* ms, i
     return SPECT_OK;
 }
 
-spect_status spect_plan_info(spect_plan P, int* separable, int* view_chunk, size_t* device_bytes)
+spect_status spect_plan_info(spect_plan P, int* separable, int* fused, int* view_chunk, size_t* device_bytes)
 {
     if (!P) return fail(SPECT_EINVAL, "plan is NULL");
     if (separable) *separable = P->separable;
+    if (fused) *fused = P->fast;
     if (view_chunk) *view_chunk = P->chunk;
     if (device_bytes) *device_bytes = P->bytes;
     return SPECT_OK;

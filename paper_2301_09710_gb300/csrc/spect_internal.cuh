@@ -73,6 +73,16 @@ struct spect_plan_s {
     int s_valid = 0;
     int cls_x = 3, cls_z = 3;    // edge classes per axis for A' (1 when the axis has length 1)
     int sep_tk = 0;              // separable kernels: k-rows per block
+    // fast path (fused kernels, k-fastest internal layout, cached attenuation)
+    int fast = 0;                // 1 when the fused kernels serve this plan
+    int bucket = 0;              // padded tap count of the fused kernels
+    int fused_J = 8;             // depth planes per fused block
+    float* mubar = nullptr;      // nview * ny*nx*nz, [l][j][i][k]
+    float* xt = nullptr;         // nx*ny*nz, [j][i][k] image
+    float* et = nullptr;         // nx*ny*nz, [j][i][k] back-projection accumulator
+    float* st = nullptr;         // nx*ny*nz, [j][i][k] sensitivity
+    float* part = nullptr;       // G * nx*nz*nview forward partial sums
+    spect::AdjEntry* adjf = nullptr;  // nview*nx*ny*adj_max fixed-length lists
     size_t bytes = 0;
     // launch accounting and optional per-launch event timing
     long long launches[SPECT_K_COUNT] = {0, 0, 0, 0, 0};
@@ -185,6 +195,18 @@ cudaError_t launch_conv_forward(const spect_plan_s& P, float* v, int l0, int nv,
 cudaError_t launch_conv_adjoint(const spect_plan_s& P, const float* v, int l0, int nv, cudaStream_t st);
 cudaError_t launch_psf_variants(spect_plan_s& P, float* scratch, cudaStream_t st);
 int choose_sep_tile(const Geometry& g, int cls_z, size_t smem_limit);
+// fast path (fused.cu)
+int fused_bucket(const Geometry& g, size_t smem_limit);
+int fused_groups(const spect_plan_s& P);
+cudaError_t launch_transpose(const float* in, float* out, int R, int C, cudaStream_t st);
+cudaError_t launch_mubar_cache(const spect_plan_s& P, const float* mu_t, cudaStream_t st);
+cudaError_t launch_build_adjacency_fixed(const spect_plan_s& P, cudaStream_t st);
+cudaError_t launch_fused_forward(const spect_plan_s& P, const float* xt, int l0, int nv, cudaStream_t st);
+cudaError_t launch_fused_adjoint(const spect_plan_s& P, const float* v, int l0, int nv, cudaStream_t st);
+cudaError_t launch_fwd_reduce(const spect_plan_s& P, float* v, const float* em_y, const float* em_rbar,
+                              cudaStream_t st);
+cudaError_t launch_adj_rot_t(const spect_plan_s& P, int l0, int nv, float* out, int accumulate, float* em_x,
+                             const float* em_s, cudaStream_t st);
 bool direct_fits(const Geometry& g, size_t smem_limit);
 cudaError_t launch_fill(float* p, size_t n, float value, cudaStream_t st);
 

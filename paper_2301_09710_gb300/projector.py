@@ -37,11 +37,19 @@ def _stream_handle(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def fp32_peak(stream=None) -> dict:
+    """Measured FP32 FMA throughput of the current device (TFLOP/s), scalar and packed."""
+    lib = _lib.load()
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _lib.check(lib.spect_fp32_peak(ctypes.byref(a), ctypes.byref(b), _stream_handle(stream)))
+    return {"ffma_tflops": a.value, "ffma2_tflops": b.value}
+
+
 class SpectPlan:
     """The operator A of one geometry (Algorithm 1 inputs) on one GPU."""
 
     def __init__(self, nx: int, nz: int, nview: int, mu=None, dy: float = 1.0, psf=None, fx=None, fz=None,
-                 angles=None, prefer_separable: bool = True, device=None, stream=None):
+                 angles=None, prefer_separable: bool = True, low_memory: bool = False, device=None, stream=None):
         self.lib = _lib.load()
         self.device = torch.device(device if device is not None else "cuda")
         self.nx = self.ny = int(nx)
@@ -61,7 +69,8 @@ class SpectPlan:
             self._angles = np.ascontiguousarray(np.asarray(angles, dtype=np.float64))
             ang = self._angles.ctypes.data_as(ctypes.c_void_p)
         handle = ctypes.c_void_p()
-        flags = _lib.SPECT_PLAN_PREFER_SEPARABLE if prefer_separable else 0
+        flags = (_lib.SPECT_PLAN_PREFER_SEPARABLE if prefer_separable else 0) | \
+            (_lib.SPECT_PLAN_LOW_MEMORY if low_memory else 0)
         with torch.cuda.device(self.device):
             _lib.check(self.lib.spect_plan_create(
                 ctypes.byref(handle), self.nx, self.ny, self.nz, self.nview, _ptr(self._mu), ctypes.c_float(dy),
@@ -122,10 +131,13 @@ class SpectPlan:
         return s
 
     def info(self) -> dict:
-        sep, chunk = ctypes.c_int(), ctypes.c_int()
+        """separable: separable-factor kernels; view_chunk: views per slab pass; device_bytes: plan memory."""
+        sep, fused, chunk = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         nbytes = ctypes.c_size_t()
-        _lib.check(self.lib.spect_plan_info(self.handle, ctypes.byref(sep), ctypes.byref(chunk), ctypes.byref(nbytes)))
-        return {"separable": bool(sep.value), "view_chunk": chunk.value, "device_bytes": nbytes.value}
+        _lib.check(self.lib.spect_plan_info(self.handle, ctypes.byref(sep), ctypes.byref(fused), ctypes.byref(chunk),
+                                            ctypes.byref(nbytes)))
+        return {"separable": bool(sep.value), "fused": bool(fused.value), "view_chunk": chunk.value,
+                "device_bytes": nbytes.value}
 
     def profile(self, enable: bool = True) -> None:
         """Bracket every later kernel launch with CUDA events on its stream."""

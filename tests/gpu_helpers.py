@@ -38,17 +38,23 @@ def host(t):
     return t.detach().cpu().numpy().astype(np.float64)
 
 
-def make_plan(prob, angles, separable, nview=None):
+# the three code paths of the library: fused kernels (separable PSF, default),
+# low-memory kernels (separable PSF), full-PSF kernels
+PATHS = ["fused", "lowmem", "direct"]
+
+
+def make_plan(prob, angles, path, nview=None):
     from paper_2301_09710_gb300 import SpectPlan
     nz, ny, nx = prob.x.shape
     nview = len(angles) if nview is None else nview
-    if separable:
-        return SpectPlan(nx, nz, nview, mu=prob.mu, dy=prob.dy, fx=prob.fx, fz=prob.fz, angles=angles)
+    if path in ("fused", "lowmem", True):
+        return SpectPlan(nx, nz, nview, mu=prob.mu, dy=prob.dy, fx=prob.fx, fz=prob.fz, angles=angles,
+                         low_memory=(path == "lowmem"))
     return SpectPlan(nx, nz, nview, mu=prob.mu, dy=prob.dy, psf=prob.full_psf(), angles=angles)
 
 
-def oracle_psf(prob, separable):
+def oracle_psf(prob, path):
     import oracle
-    if separable:
+    if path in ("fused", "lowmem", True):
         return oracle.psf_from_factors(prob.fx, prob.fz)
     return prob.full_psf().astype(np.float64)

@@ -55,7 +55,7 @@ def test_calls_reject_null_plan_and_pointers(lib):
     assert "plan is NULL" in _lib.last_error()
     assert lib.spect_back(None, 16, 16, None) == 1
     assert lib.spect_em_step(None, 16, 16, None, 1, None) == 1
-    assert lib.spect_plan_info(None, None, None, None) == 1
+    assert lib.spect_plan_info(None, None, None, None, None) == 1
     assert lib.spect_plan_destroy(None) == 0
 
 

@@ -13,7 +13,7 @@ import pytest
 import oracle
 from paper_2301_09710_gb300 import synthetic
 
-from gpu_helpers import ADJ_FP32, assert_close, dev, host, make_plan, need_gpu, oracle_psf, torch
+from gpu_helpers import ADJ_FP32, PATHS, assert_close, dev, host, make_plan, need_gpu, oracle_psf, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -26,13 +26,14 @@ def prob():
     return synthetic.config2(seed=0)
 
 
-@pytest.mark.parametrize("separable", [True, False])
-def test_config2_sampled_views(prob, separable):
+@pytest.mark.parametrize("path", PATHS)
+def test_config2_sampled_views(prob, path):
     ang = oracle.default_angles(128)
-    plan = make_plan(prob, ang, separable)
+    plan = make_plan(prob, ang, path)
+    assert plan.info()["fused"] == (path == "fused")
     x = dev(prob.x)
     v = host(plan.forward(x))
-    psf = oracle_psf(prob, separable)
+    psf = oracle_psf(prob, path)
     sub = ang[SAMPLE_VIEWS]
     v_o = oracle.forward(prob.x, prob.mu, psf, prob.dy, sub, nthreads=4)
     assert_close(v[SAMPLE_VIEWS], v_o, what="A x sampled views")
@@ -46,9 +47,10 @@ def test_config2_sampled_views(prob, separable):
     plan.close()
 
 
-def test_config2_adjoint_and_em_invariants(prob):
+@pytest.mark.parametrize("path", ["fused", "lowmem"])
+def test_config2_adjoint_and_em_invariants(prob, path):
     ang = oracle.default_angles(128)
-    plan = make_plan(prob, ang, True)
+    plan = make_plan(prob, ang, path)
     x = dev(prob.x)
     v = plan.forward(x)
     rng = np.random.default_rng(6)
@@ -75,11 +77,12 @@ def test_config2_adjoint_and_em_invariants(prob):
     plan.close()
 
 
-def test_config2_geometry_em_step_vs_oracle(prob):
+@pytest.mark.parametrize("path", ["fused", "lowmem"])
+def test_config2_geometry_em_step_vs_oracle(prob, path):
     views = [3, 40, 77, 120]
     ang = oracle.default_angles(128)[views]
-    plan = make_plan(prob, ang, True)
-    psf = oracle_psf(prob, True)
+    plan = make_plan(prob, ang, path)
+    psf = oracle_psf(prob, path)
     xt = prob.x
     ybar = oracle.forward(xt, prob.mu, psf, prob.dy, ang, nthreads=4)
     scale = 1e7 / ybar.sum()

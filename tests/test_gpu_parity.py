@@ -10,7 +10,7 @@ import pytest
 import oracle
 from paper_2301_09710_gb300 import synthetic
 
-from gpu_helpers import (ADJ_FP32, assert_close, dev, host, make_plan, need_gpu, oracle_psf, torch)
+from gpu_helpers import (ADJ_FP32, PATHS, assert_close, dev, host, make_plan, need_gpu, oracle_psf, torch)
 
 pytestmark = pytest.mark.gpu
 
@@ -21,13 +21,13 @@ def _gpu():
 
 
 # ---------------------------------------------------------------- config-1 workload, full size
-@pytest.mark.parametrize("separable", [True, False])
-def test_config1_forward_back_em(separable):
+@pytest.mark.parametrize("path", PATHS)
+def test_config1_forward_back_em(path):
     prob = synthetic.config1(seed=0)
     ang = oracle.default_angles(prob.nview)
-    psf = oracle_psf(prob, separable)
-    plan = make_plan(prob, ang, separable)
-    assert plan.info()["separable"] == separable
+    psf = oracle_psf(prob, path)
+    plan = make_plan(prob, ang, path)
+    assert plan.info()["separable"] == (path != "direct")
     x = dev(prob.x)
     v = plan.forward(x)
     v_o = oracle.forward(prob.x, prob.mu, psf, prob.dy, ang)
@@ -63,16 +63,16 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("separable", [True, False])
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}x{c[1]}v{c[2]}p{c[3]}x{c[4]}" for c in CASES])
-def test_ragged_forward_back(case, separable):
+def test_ragged_forward_back(case, path):
     nx, nz, nview, px, pz, nvp, seed = case
     prob = synthetic.random_problem(seed, nx=nx, nz=nz, nview=nview, px=px, pz=pz, nview_psf=nvp, mu_scale=0.1)
     rng = np.random.default_rng(seed)
     ang = rng.uniform(0, 2 * np.pi, nview)
     ang[0] = np.pi / 2  # always include an exact quarter turn
-    psf = oracle_psf(prob, separable)
-    plan = make_plan(prob, ang, separable)
+    psf = oracle_psf(prob, path)
+    plan = make_plan(prob, ang, path)
     v = plan.forward(dev(prob.x))
     v_o = oracle.forward(prob.x, prob.mu, psf, prob.dy, ang)
     assert_close(host(v), v_o, what="A x")
@@ -83,24 +83,27 @@ def test_ragged_forward_back(case, separable):
     plan.close()
 
 
-def test_no_attenuation_map():
+@pytest.mark.parametrize("low_memory", [False, True])
+def test_no_attenuation_map(low_memory):
     prob = synthetic.random_problem(6, nx=24, nz=8, nview=5, px=5, pz=5)
     ang = oracle.default_angles(5)
     from paper_2301_09710_gb300 import SpectPlan
-    plan = SpectPlan(24, 8, 5, mu=None, dy=1.0, fx=prob.fx, fz=prob.fz, angles=ang)
+    plan = SpectPlan(24, 8, 5, mu=None, dy=1.0, fx=prob.fx, fz=prob.fz, angles=ang, low_memory=low_memory)
     v = plan.forward(dev(prob.x))
     v_o = oracle.forward(prob.x, np.zeros_like(prob.x), oracle.psf_from_factors(prob.fx, prob.fz), 1.0, ang)
     assert_close(host(v), v_o, what="A x, mu = 0")
 
 
-def test_quarter_turns_exact_line_sums():
+@pytest.mark.parametrize("low_memory", [False, True])
+def test_quarter_turns_exact_line_sums(low_memory):
     # mu = 0, delta PSF, views at multiples of 90 degrees: rotated line sums
     n, nz = 16, 5
     rng = np.random.default_rng(7)
     x = rng.integers(0, 8, (nz, n, n)).astype(np.float32)  # small integers: sums are exact in FP32
     from paper_2301_09710_gb300 import SpectPlan
     fx = np.zeros((1, n, 1), np.float32) + 1
-    plan = SpectPlan(n, nz, 4, mu=None, dy=1.0, fx=fx, fz=fx.copy(), angles=np.arange(4) * np.pi / 2)
+    plan = SpectPlan(n, nz, 4, mu=None, dy=1.0, fx=fx, fz=fx.copy(), angles=np.arange(4) * np.pi / 2,
+                     low_memory=low_memory)
     v = host(plan.forward(dev(x)))
     for q in range(4):
         want = np.stack([np.rot90(x[k], -q).sum(axis=0) for k in range(nz)])
@@ -108,11 +111,11 @@ def test_quarter_turns_exact_line_sums():
 
 
 # ---------------------------------------------------------------- the paper's adjoint experiment
-@pytest.mark.parametrize("separable", [True, False])
-def test_dense_adjoint_paper_shape_fp32(separable):
+@pytest.mark.parametrize("path", PATHS)
+def test_dense_adjoint_paper_shape_fp32(path):
     prob = synthetic.random_problem(100, nx=8, nz=6, nview=7, px=3, pz=3, symmetric=True, mu_scale=0.3)
     ang = oracle.default_angles(7)
-    plan = make_plan(prob, ang, separable)
+    plan = make_plan(prob, ang, path)
     N, M = 8 * 8 * 6, 8 * 6 * 7
     eye_n = torch.eye(N, device="cuda", dtype=torch.float32)
     eye_m = torch.eye(M, device="cuda", dtype=torch.float32)
@@ -122,17 +125,18 @@ def test_dense_adjoint_paper_shape_fp32(separable):
     err = np.linalg.norm(A.T - B) / np.linalg.norm(A)
     assert err < 1e-6, err  # the paper's FP32 figure (Section III-A)
     # and the dense matrix itself against the oracle's
-    psf = oracle_psf(prob, separable)
+    psf = oracle_psf(prob, path)
     A_o = np.stack([oracle.forward(e.reshape(6, 8, 8), prob.mu, psf, 1.0, ang, nthreads=1).ravel()
                     for e in np.eye(N)], axis=1)
     assert np.linalg.norm(A - A_o) / np.linalg.norm(A_o) < 2e-6
 
 
 # ---------------------------------------------------------------- determinism
-def test_bitwise_deterministic():
+@pytest.mark.parametrize("path", PATHS)
+def test_bitwise_deterministic(path):
     prob = synthetic.config1(seed=2, nx=32, nz=16, nview=16)
     ang = oracle.default_angles(16)
-    plan = make_plan(prob, ang, True)
+    plan = make_plan(prob, ang, path)
     x = dev(prob.x)
     a = host(plan.forward(x))
     b = host(plan.forward(x))
@@ -142,10 +146,11 @@ def test_bitwise_deterministic():
     np.testing.assert_array_equal(c, d)
 
 
-def test_sensitivity_matches_oracle():
+@pytest.mark.parametrize("path", PATHS)
+def test_sensitivity_matches_oracle(path):
     prob = synthetic.config1(seed=3, nx=32, nz=12, nview=10, psf_size=7)
     ang = oracle.default_angles(10)
-    plan = make_plan(prob, ang, True)
+    plan = make_plan(prob, ang, path)
     s = host(plan.sensitivity())
-    s_o = oracle.sensitivity(prob.mu, oracle_psf(prob, True), prob.dy, ang)
+    s_o = oracle.sensitivity(prob.mu, oracle_psf(prob, path), prob.dy, ang)
     assert_close(s, s_o, what="A'1")
