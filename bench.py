@@ -123,11 +123,20 @@ def make_workload(device, path):
     return prob, plan, x0, y, rbar
 
 
-def algorithmic_flops(kind: str, nv: int, sep: bool) -> float:
-    """Algorithmic FLOPs of one launch of a kernel class that processes nv views."""
+def algorithmic_flops(kind: str, nv: float, sep: bool, fused: bool = False) -> float:
+    """Algorithmic FLOPs of one launch of a kernel class that processes nv views.
+
+    Per voxel-view: blur 2(px+pz) (separable) or 2 px pz (full PSF); bilinear
+    rotation 7 (4 mul + 3 add); attenuation multiply 1; depth or view sum 1;
+    adjoint rotation 8 (4 weighted adds).  The fused forward kernel also
+    rotates and attenuates (7 + 1 + 1 on top of the blur); the low-memory
+    rotate kernel also rebuilds the attenuation (~20 in all).
+    """
     vv = float(NX) * NX * NZ * nv  # voxel-views
     conv = 2.0 * (PSF + PSF) if sep else 2.0 * PSF * PSF
-    return {"conv_fwd": conv * vv, "conv_adj": conv * vv, "rotate_atten": 20.0 * vv, "rotate_adj": 8.0 * vv}.get(kind, 0.0)
+    per = {"conv_fwd": conv + (9.0 if fused else 1.0), "conv_adj": conv + 1.0,
+           "rotate_atten": 20.0, "rotate_adj": 8.0}.get(kind, 0.0)
+    return per * vv
 
 
 def peaks(torch, dev_index):
@@ -156,7 +165,9 @@ def run_ours(args):
     build()
 
     prob, plan, x0_h, y_h, rbar_h = make_workload(device, args.path)
-    sep = plan.info()["separable"]
+    info = plan.info()
+    sep = info["separable"]
+    chunk = info["view_chunk"]
     y = torch.from_numpy(y_h).to(device)
     rbar = torch.from_numpy(rbar_h).to(device)
     x = torch.from_numpy(x0_h).to(device)
@@ -204,14 +215,12 @@ def run_ours(args):
     pk = peaks(torch, local)
     from paper_2301_09710_gb300.projector import fp32_peak
     probe = fp32_peak()
-    info = plan.info()
-    chunk = info["view_chunk"]
     kern = {}
     for k, (n, ms) in prof.items():
         if n == 0:
             continue
         nv_avg = NVIEW * args.steps / n if k != "other" else 0
-        fl = algorithmic_flops(k, nv_avg, sep) if k != "other" else 0.0
+        fl = algorithmic_flops(k, nv_avg, sep, info["fused"]) if k != "other" else 0.0
         kern[k] = {"launches": n, "ms_total": ms, "ms_avg": ms / n, "share": None,
                    "tflops": (fl / (ms / n * 1e-3) / 1e12) if ms > 0 and fl else None}
     tot = sum(v["ms_total"] for v in kern.values())
