@@ -114,8 +114,9 @@ cudaError_t launch_mubar_cache(const spect_plan_s& P, const float* mu_t, cudaStr
 }
 
 // Fixed-length adjacency lists for the transposed rotation: for destination
-// q and view l, up to `maxe` (source pixel p, weight) pairs, zero-padded.  The
-// candidate search and weights are those of k_build_adjacency (rotate.cu).
+// q and view l, up to `maxe` (source column offset p*nz, weight) pairs,
+// zero-padded, laid out [q][l][e].  The candidate search and weights are those
+// of k_build_adjacency (rotate.cu).
 __global__ void k_build_adjacency_fixed(Geometry g, const ViewRot* __restrict__ rot, int maxe, AdjEntry* adj)
 {
     const size_t nxy = (size_t)g.nx * g.ny;
@@ -131,7 +132,7 @@ __global__ void k_build_adjacency_fixed(Geometry g, const ViewRot* __restrict__ 
     const float pi_ = c + ct * dqi - st * dqj;
     const float pj_ = c + st * dqi + ct * dqj;
     const int bi = (int)floorf(pi_) - 1, bj = (int)floorf(pj_) - 1;
-    AdjEntry* out = adj + idx * maxe;
+    AdjEntry* out = adj + ((size_t)q * g.nview + l) * maxe;
     int cnt = 0;
     for (int cj = 0; cj < 4; ++cj)
         for (int ci = 0; ci < 4; ++ci) {
@@ -143,7 +144,7 @@ __global__ void k_build_adjacency_fixed(Geometry g, const ViewRot* __restrict__ 
             const float w = bilinear_w(s, di, dj);
             if (w == 0.f || cnt >= maxe) continue;
             AdjEntry e;
-            e.p = pi + g.nx * pj;
+            e.p = (pi + g.nx * pj) * g.nz;  // offset of the source column in a [j][i][k] slab
             e.w = w;
             out[cnt++] = e;
         }
@@ -176,7 +177,6 @@ struct Sep {
 };
 
 constexpr int kFusedThreads = 640;
-constexpr int kMaxZ = 4;  // k-pass items per thread
 
 // Shared-memory plan of a fused kernel, computed identically on host and device.
 struct FusedDims {
@@ -188,9 +188,10 @@ struct FusedDims {
     int J, G;   // depth planes per block, depth groups
 };
 
-__host__ __device__ inline size_t fused_smem_floats(const FusedDims& d, int nx, int PT)
+__host__ __device__ inline size_t fused_smem_floats(const FusedDims& d, int nx, int nz, int PT)
 {
-    return (size_t)d.warea + (size_t)nx * d.kpu + 6 * (size_t)PT + 5 * (size_t)nx;
+    // W | U | taps (6 PT) | rotation table (5 nx) | depth-sum accumulators (nx*nz, forward only)
+    return (size_t)d.warea + (size_t)nx * d.kpu + 6 * (size_t)PT + 5 * (size_t)nx + (size_t)nx * nz;
 }
 
 template <int P>
@@ -212,6 +213,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
     float* FZ = FX + PT;
     float4* TW = reinterpret_cast<float4*>(FZ + PT);  // nx weights (16-byte aligned: offsets are multiples of 4)
     int* TB = reinterpret_cast<int*>(TW + nx);        // nx bases
+    float* ACC = reinterpret_cast<float*>(TB + nx);   // nz x nx depth-sum accumulators [k][i]
     const int tid = threadIdx.x;
     const int T = kFusedThreads;
     const int grp = blockIdx.x, l = l0 + blockIdx.y;
@@ -221,11 +223,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
     const int ox = (P - g.px) / 2, oz = (P - g.pz) / 2;  // zero-padding offsets of the taps
     const size_t pln = (size_t)nx * nz;
 
-    float acc[kMaxZ][CZ];
-#pragma unroll
-    for (int q = 0; q < kMaxZ; ++q)
-#pragma unroll
-        for (int c = 0; c < CZ; ++c) acc[q][c] = 0.f;
+    for (int e = tid; e < nx * nz; e += T) ACC[e] = 0.f;
 
     for (int j = j_begin; j < j_end; ++j) {
         // taps (zero-padded to P, centred) and the rotation table of row j
@@ -237,22 +235,56 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
         for (int i = tid; i < nx; i += T) rot_table_entry(i, j, r, g, TW[i], TB[i]);
         __syncthreads();
 
-        // rotate + attenuate the (i,k) plane into W (rows C..C+nx-1), replicate halo rows
-        const float* mb = mubar + ((size_t)l * ny + j) * pln;
-        for (int f = tid; f < nx * nz; f += T) {
-            const int i = f / nz, k = f - i * nz;
-            const float4 w = TW[i];
-            const float* xb = xt + (size_t)TB[i] * nz + k;
-            float v = w.x * __ldg(xb);
-            v = fmaf(w.y, __ldg(xb + nz), v);
-            v = fmaf(w.z, __ldg(xb + pln), v);
-            v = fmaf(w.w, __ldg(xb + pln + nz), v);
-            v *= __ldg(mb + f);
-            W[(C + i) * d.kpw + k] = v;
-            if (i == 0)
-                for (int h = 0; h < C; ++h) W[h * d.kpw + k] = v;
-            if (i == nx - 1)
-                for (int h = C + nx; h < d.wrows; ++h) W[h * d.kpw + k] = v;
+        // rotate + attenuate the (i,k) plane into W (rows C..C+nx-1), replicate
+        // halo rows; four points per thread per batch keep 20 loads in flight
+        {
+            const float* mb = mubar + ((size_t)l * ny + j) * pln;
+            const int nf = nx * nz;
+            const int sdi = T / nz, sdk = T - sdi * nz;  // (i,k) step of one stride T
+            int ci = tid / nz, ck = tid - ci * nz;
+            for (int f0 = tid; f0 < nf; f0 += 4 * T) {
+                float xv[4][4], mv[4];
+                int ii[4], kk[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int f = f0 + u * T;
+                    ii[u] = ci;
+                    kk[u] = ck;
+                    ck += sdk;
+                    ci += sdi;
+                    if (ck >= nz) {
+                        ck -= nz;
+                        ++ci;
+                    }
+                    if (f < nf) {
+                        const float* xb = xt + (size_t)TB[ii[u]] * nz + kk[u];
+                        xv[u][0] = __ldg(xb);
+                        xv[u][1] = __ldg(xb + nz);
+                        xv[u][2] = __ldg(xb + pln);
+                        xv[u][3] = __ldg(xb + pln + nz);
+                        mv[u] = __ldg(mb + f);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int f = f0 + u * T;
+                    if (f < nf) {
+                        const float4 w = TW[ii[u]];
+                        float v = w.x * xv[u][0];
+                        v = fmaf(w.y, xv[u][1], v);
+                        v = fmaf(w.z, xv[u][2], v);
+                        v = fmaf(w.w, xv[u][3], v);
+                        W[(C + ii[u]) * d.kpw + kk[u]] = v * mv[u];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // replicate padding along i: halo rows copy the first/last plane row
+        for (int e = tid; e < nz; e += T) {
+            const float lo = W[C * d.kpw + e], hi = W[(C + nx - 1) * d.kpw + e];
+            for (int h = 0; h < C; ++h) W[h * d.kpw + e] = lo;
+            for (int h = C + nx; h < d.wrows; ++h) W[h * d.kpw + e] = hi;
         }
         __syncthreads();
 
@@ -280,25 +312,28 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
                 }
             }
 #pragma unroll
-            for (int c = 0; c < CX; ++c) {
-                const int i = i0 + c;
-                if (i < nx) {
-                    float* ur = U + (size_t)i * d.kpu;
-                    ur[ZH + k] = o[c];
-                    if (k == 0)
-                        for (int h = 0; h < ZH; ++h) ur[h] = o[c];
-                    if (k == nz - 1)
-                        for (int h = ZH + nz; h < d.kpu; ++h) ur[h] = o[c];
+            for (int c = 0; c < CX; ++c)
+                if (i0 + c < nx) U[(size_t)(i0 + c) * d.kpu + ZH + k] = o[c];
+        }
+        __syncthreads();
+        // replicate padding along k: halo columns copy the first/last column (warp per row)
+        {
+            const int lane = tid & 31, warp = tid >> 5, nwarp = T >> 5;
+            const int nh = d.kpu - nz;  // ZH left + the rest right
+            for (int i = warp; i < nx; i += nwarp) {
+                float* ur = U + (size_t)i * d.kpu;
+                const float lo = ur[ZH], hi = ur[ZH + nz - 1];
+                for (int h = lane; h < nh; h += 32) {
+                    if (h < ZH) ur[h] = lo;
+                    else ur[nz + h] = hi;
                 }
             }
         }
         __syncthreads();
 
-        // k-pass into the register partial sums: lanes over i
-#pragma unroll
-        for (int q = 0; q < kMaxZ; ++q) {
-            const int it = tid + q * T;
-            if (it < nx * d.nkb) {
+        // k-pass into the depth-sum accumulators: lanes over i
+        for (int it = tid; it < nx * d.nkb; it += T) {
+            {
                 const int kb = it / nx, i = it - kb * nx;
                 const float4* row = reinterpret_cast<const float4*>(U + (size_t)i * d.kpu + kb * CZ);
                 float win[WZ];
@@ -327,25 +362,16 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
                     }
                 }
 #pragma unroll
-                for (int c = 0; c < CZ; ++c) acc[q][c] += o[c];
+                for (int c = 0; c < CZ; ++c)
+                    if (kb * CZ + c < nz) ACC[(kb * CZ + c) * nx + i] += o[c];
             }
         }
         __syncthreads();
     }
 
     // partial depth sums of this group: part[grp][l][k][i]
-#pragma unroll
-    for (int q = 0; q < kMaxZ; ++q) {
-        const int it = tid + q * T;
-        if (it < nx * d.nkb) {
-            const int kb = it / nx, i = it - kb * nx;
-#pragma unroll
-            for (int c = 0; c < CZ; ++c) {
-                const int k = kb * CZ + c;
-                if (k < nz) part[(((size_t)grp * g.nview + l) * nz + k) * nx + i] = acc[q][c];
-            }
-        }
-    }
+    float* pout = part + ((size_t)grp * g.nview + l) * nz * nx;
+    for (int e = tid; e < nx * nz; e += T) pout[e] = ACC[e];
 }
 
 // v(i,k,l) = sum over depth groups of the partials (fixed order), optionally
@@ -467,6 +493,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
         for (int it = tid; it < nz * d.nib; it += T) {
             const int ib = it / nz, k = it - ib * nz;
             const int i0 = ib * CX;
+            float mbv[CX];
+#pragma unroll
+            for (int c = 0; c < CX; ++c) mbv[c] = (i0 + c < nx) ? __ldg(mb + (size_t)(i0 + c) * nz + k) : 0.f;
             float win[CX + P - 1];
 #pragma unroll
             for (int m = 0; m < CX + P - 1; ++m) win[m] = Zb[(i0 + m) * d.kpw + k];
@@ -496,38 +525,71 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
                     for (int a = 0; a < P; ++a) s = fmaf(f[a], win[c + a], s);
                     o[c] = s;
                 }
-                if (i < nx) tout[(size_t)i * nz + k] = o[c] * __ldg(mb + (size_t)i * nz + k);
+                if (i < nx) tout[(size_t)i * nz + k] = o[c] * mbv[c];
             }
         }
         __syncthreads();
     }
 }
 
-// x_t(q,k) (+)= sum_{v in chunk} sum_{e < maxe} w_e t[v][p_e][k]  (lanes over k)
-// with the MLEM update x <- x e / s on the last chunk when em_x is set.
-__global__ void __launch_bounds__(256) k_adj_rot_t(Geometry g, int maxe, const AdjEntry* __restrict__ adj,
+// x_t(q,k) (+)= sum_{v in chunk} sum_{e < MAXE} w_e t[v][p_e][k]  (lanes over k)
+// with the MLEM update x <- x e / s on the last chunk when em_x is set.  The
+// lists are laid out [q][l][e] so one destination's entries for all views are
+// contiguous; each entry holds the premultiplied offset p*nz of its source
+// column.  Per view the few terms are summed plainly, the views with Kahan.
+template <int MAXE>
+__global__ void __launch_bounds__(256) k_adj_rot_t(Geometry g, const AdjEntry* __restrict__ adj,
                                                    const float* __restrict__ slab, int l0, int nv, float* out,
                                                    int accumulate, float* em_x, const float* __restrict__ em_s)
 {
-    const size_t nxy = (size_t)g.nx * g.ny;
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nxy = g.nx * g.ny;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= nxy * g.nz) return;
-    const size_t q = idx / g.nz;
-    const int k = (int)(idx - q * g.nz);
+    const int q = idx / g.nz;
+    const int k = idx - q * g.nz;
+    const AdjEntry* e = adj + ((size_t)q * g.nview + l0) * MAXE;
+    const float* t = slab + k;
+    const size_t vstride = (size_t)nxy * g.nz;
     KSum acc;
-    for (int v = 0; v < nv; ++v) {
-        const AdjEntry* e = adj + ((size_t)(l0 + v) * nxy + q) * maxe;
-        const float* t = slab + (size_t)v * nxy * g.nz + k;
-        for (int m = 0; m < maxe; ++m) {
-            const AdjEntry a = e[m];
-            acc.add(a.w * __ldg(t + (size_t)a.p * g.nz));
+    int v = 0;
+    for (; v + 1 < nv; v += 2) {
+        AdjEntry a0[MAXE], a1[MAXE];
+#pragma unroll
+        for (int m = 0; m < MAXE; ++m) {
+            a0[m] = e[m];
+            a1[m] = e[MAXE + m];
         }
+        float t0[MAXE], t1[MAXE];
+#pragma unroll
+        for (int m = 0; m < MAXE; ++m) {
+            t0[m] = __ldg(t + a0[m].p);
+            t1[m] = __ldg(t + vstride + a1[m].p);
+        }
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int m = 0; m < MAXE; ++m) {
+            s0 = fmaf(a0[m].w, t0[m], s0);
+            s1 = fmaf(a1[m].w, t1[m], s1);
+        }
+        acc.add(s0);
+        acc.add(s1);
+        e += 2 * MAXE;
+        t += 2 * vstride;
+    }
+    if (v < nv) {
+        float s0 = 0.f;
+#pragma unroll
+        for (int m = 0; m < MAXE; ++m) {
+            const AdjEntry a = e[m];
+            s0 = fmaf(a.w, __ldg(t + a.p), s0);
+        }
+        acc.add(s0);
     }
     float val = acc.value();
     if (accumulate) val += out[idx];
     if (em_x) {
-        const float s = em_s[idx];
-        em_x[idx] = s > 0.f ? (em_x[idx] * val) / s : 0.f;
+        const float sv = em_s[idx];
+        em_x[idx] = sv > 0.f ? (em_x[idx] * val) / sv : 0.f;
     } else {
         out[idx] = val;
     }
@@ -561,14 +623,14 @@ FusedDims dims_for(const Geometry& g, int J)
 template <int P>
 size_t smem_for(const Geometry& g, const FusedDims& d)
 {
-    return fused_smem_floats(d, g.nx, Sep<P>::PT) * sizeof(float);
+    return fused_smem_floats(d, g.nx, g.nz, Sep<P>::PT) * sizeof(float);
 }
 
 template <int P>
 bool fits(const Geometry& g, size_t limit)
 {
     const FusedDims d = dims_for<P>(g, 8);
-    return smem_for<P>(g, d) <= limit && (size_t)g.nx * d.nkb <= (size_t)kFusedThreads * kMaxZ;
+    return smem_for<P>(g, d) <= limit;
 }
 
 template <int P>
@@ -658,8 +720,16 @@ cudaError_t launch_adj_rot_t(const spect_plan_s& P, int l0, int nv, float* out, 
                              const float* em_s, cudaStream_t st)
 {
     const size_t n = (size_t)P.g.nx * P.g.ny * P.g.nz;
-    k_adj_rot_t<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.g, P.adj_max, P.adjf, P.slab, l0, nv, out, accumulate,
-                                                            em_x, em_s);
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    switch (P.adj_max) {
+#define SPECT_ADJ(M)                                                                                             \
+    case M:                                                                                                      \
+        k_adj_rot_t<M><<<blocks, 256, 0, st>>>(P.g, P.adjf, P.slab, l0, nv, out, accumulate, em_x, em_s); \
+        break;
+        SPECT_ADJ(1) SPECT_ADJ(2) SPECT_ADJ(3) SPECT_ADJ(4) SPECT_ADJ(5) SPECT_ADJ(6) SPECT_ADJ(7) SPECT_ADJ(8)
+#undef SPECT_ADJ
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

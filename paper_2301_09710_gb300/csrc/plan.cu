@@ -281,6 +281,7 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
     for (const void* p : ins)
         if (p && !aligned16(p)) return fail(SPECT_EINVAL, "device inputs must be 16-byte aligned");
     if ((size_t)nview * nx * ny * 6 >= (size_t)INT32_MAX) return fail(SPECT_EUNSUPPORTED, "nview*nx*ny too large");
+    if ((size_t)nx * ny * nz >= (size_t)INT32_MAX / 2) return fail(SPECT_EUNSUPPORTED, "nx*ny*nz too large");
     if (angles)
         for (int l = 0; l < nview; ++l)
             if (!isfinite(angles[l])) return fail(SPECT_EINVAL, "angles must be finite");
@@ -408,6 +409,7 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
         PLAN_TRY(e3, "adjacency max download");
         PLAN_TRY(e4, "adjacency count");
         P->adj_max = mx;
+        if (P->fast && mx > 8) P->fast = 0;  // fixed-length lists are instantiated up to 8 entries
         if (P->fast) {
             PLAN_ALLOC(P->adjf, nlist * (size_t)std::max(mx, 1), "adjacency lists");
             if (mx < 1) P->adj_max = 1;
