@@ -165,12 +165,22 @@ cudaError_t launch_build_adjacency_fixed(const spect_plan_s& P, cudaStream_t st)
 
 // ============================================================================
 // Fused forward, separable PSF, padded tap count P (odd).
+//
+// Shared-memory layout of one block (view l, depth group):
+//   W   nz rows x wp columns: the rotated, attenuated plane, W[k][C + i], with
+//       replicate halo columns; wp is odd so column-wise stores and the i-pass
+//       windows (lanes over k) are bank-conflict free, and every window load
+//       of the i-pass is an immediate offset from one base.
+//   U   nx rows x kpu: i-pass output, U[i][ZH + k], with replicate halo
+//       columns; kpu/4 is odd so the k-pass float4 windows (lanes over i) are
+//       bank-conflict free.
+//   ACC nz x nx depth-sum accumulators of the group, [k][i].
 // ============================================================================
 template <int P>
 struct Sep {
     static constexpr int C = (P - 1) / 2;    // tap centre
-    static constexpr int CX = 8;             // i outputs per thread (i-pass)
-    static constexpr int CZ = 8;             // k outputs per thread (k-pass)
+    static constexpr int CX = 16;            // i outputs per thread (i-pass)
+    static constexpr int CZ = 16;            // k outputs per thread (k-pass)
     static constexpr int ZH = (C + 3) & ~3;  // k halo columns, 16-byte aligned
     static constexpr int WZ = CZ + 2 * ZH;   // k-pass window (multiple of 4)
     static constexpr int PT = (P + 3) & ~3;  // tap array length
@@ -180,10 +190,9 @@ constexpr int kFusedThreads = 640;
 
 // Shared-memory plan of a fused kernel, computed identically on host and device.
 struct FusedDims {
-    int kpw;    // W row pitch (>= nz, odd: conflict-free column stores)
+    int wp;     // W row pitch (odd, >= nib*CX + 2*C)
     int warea;  // floats reserved for W (multiple of 4, keeps U 16-byte aligned)
     int kpu;    // U row pitch (>= nkb*CZ + 2*ZH, multiple of 4, pitch/4 odd)
-    int wrows;  // W rows: nib*CX + 2*C
     int nib, nkb;
     int J, G;   // depth planes per block, depth groups
 };
@@ -192,6 +201,42 @@ __host__ __device__ inline size_t fused_smem_floats(const FusedDims& d, int nx, 
 {
     // W | U | taps (6 PT) | rotation table (5 nx) | depth-sum accumulators (nx*nz, forward only)
     return (size_t)d.warea + (size_t)nx * d.kpu + 6 * (size_t)PT + 5 * (size_t)nx + (size_t)nx * nz;
+}
+
+template <int P>
+__device__ __forceinline__ void load_window_f4(const float* base, float (&win)[Sep<P>::WZ])
+{
+    const float4* row = reinterpret_cast<const float4*>(base);
+#pragma unroll
+    for (int m4 = 0; m4 < Sep<P>::WZ / 4; ++m4) {
+        const float4 t = row[m4];
+        win[4 * m4] = t.x;
+        win[4 * m4 + 1] = t.y;
+        win[4 * m4 + 2] = t.z;
+        win[4 * m4 + 3] = t.w;
+    }
+}
+
+// o[c] = sum_b taps[b] win[c + SIGN*b + OFF]   (SIGN = -1: convolution, +1: correlation)
+template <int P, int N, int SIGN, int OFF, int WN>
+__device__ __forceinline__ void fir(const float* taps, const float (&win)[WN], float (&o)[N])
+{
+    constexpr int PT = Sep<P>::PT;
+#pragma unroll
+    for (int c = 0; c < N; ++c) o[c] = 0.f;
+#pragma unroll
+    for (int b4 = 0; b4 < PT / 4; ++b4) {
+        const float4 f4 = reinterpret_cast<const float4*>(taps)[b4];
+        const float fv[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int b = 4 * b4 + u;
+            if (b < P) {
+#pragma unroll
+                for (int c = 0; c < N; ++c) o[c] = fmaf(fv[u], win[c + SIGN * b + OFF], o[c]);
+            }
+        }
+    }
 }
 
 template <int P>
@@ -207,21 +252,22 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
     constexpr int C = S::C, CX = S::CX, CZ = S::CZ, ZH = S::ZH, WZ = S::WZ, PT = S::PT;
     extern __shared__ __align__(16) float sm[];
     const int nx = g.nx, ny = g.ny, nz = g.nz;
-    float* W = sm;                                   // wrows x kpw, row C+i holds plane row i
-    float* U = W + d.warea;                          // nx x kpu, column ZH+k holds k
-    float* FX = U + (size_t)nx * d.kpu;              // PT taps
+    float* W = sm;
+    float* U = W + d.warea;
+    float* FX = U + (size_t)nx * d.kpu;
     float* FZ = FX + PT;
-    float4* TW = reinterpret_cast<float4*>(FZ + PT);  // nx weights (16-byte aligned: offsets are multiples of 4)
-    int* TB = reinterpret_cast<int*>(TW + nx);        // nx bases
-    float* ACC = reinterpret_cast<float*>(TB + nx);   // nz x nx depth-sum accumulators [k][i]
-    const int tid = threadIdx.x;
-    const int T = kFusedThreads;
+    float4* TW = reinterpret_cast<float4*>(FZ + PT);
+    int* TB = reinterpret_cast<int*>(TW + nx);
+    float* ACC = reinterpret_cast<float*>(TB + nx);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int T = kFusedThreads, NW = kFusedThreads / 32;
     const int grp = blockIdx.x, l = l0 + blockIdx.y;
     const int lp = g.nvp == 1 ? 0 : l;
     const int j_begin = grp * d.J, j_end = min(ny, j_begin + d.J);
     const ViewRot r = rot[l];
     const int ox = (P - g.px) / 2, oz = (P - g.pz) / 2;  // zero-padding offsets of the taps
-    const size_t pln = (size_t)nx * nz;
+    const int pln = nx * nz;
+    const int wcols = d.nib * CX + 2 * C;  // used W columns
 
     for (int e = tid; e < nx * nz; e += T) ACC[e] = 0.f;
 
@@ -235,19 +281,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
         for (int i = tid; i < nx; i += T) rot_table_entry(i, j, r, g, TW[i], TB[i]);
         __syncthreads();
 
-        // rotate + attenuate the (i,k) plane into W (rows C..C+nx-1), replicate
-        // halo rows; four points per thread per batch keep 20 loads in flight
+        // rotate + attenuate the plane into W[k][C+i]; four points per thread
+        // per batch keep 20 independent loads in flight
         {
             const float* mb = mubar + ((size_t)l * ny + j) * pln;
-            const int nf = nx * nz;
             const int sdi = T / nz, sdk = T - sdi * nz;  // (i,k) step of one stride T
             int ci = tid / nz, ck = tid - ci * nz;
-            for (int f0 = tid; f0 < nf; f0 += 4 * T) {
+            for (int f0 = tid; f0 < pln; f0 += 4 * T) {
                 float xv[4][4], mv[4];
                 int ii[4], kk[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int f = f0 + u * T;
                     ii[u] = ci;
                     kk[u] = ck;
                     ck += sdk;
@@ -256,35 +300,37 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
                         ck -= nz;
                         ++ci;
                     }
-                    if (f < nf) {
-                        const float* xb = xt + (size_t)TB[ii[u]] * nz + kk[u];
+                    if (f0 + u * T < pln) {
+                        const float* xb = xt + (TB[ii[u]] * nz + kk[u]);
                         xv[u][0] = __ldg(xb);
                         xv[u][1] = __ldg(xb + nz);
                         xv[u][2] = __ldg(xb + pln);
                         xv[u][3] = __ldg(xb + pln + nz);
-                        mv[u] = __ldg(mb + f);
+                        mv[u] = __ldg(mb + f0 + u * T);
                     }
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int f = f0 + u * T;
-                    if (f < nf) {
+                    if (f0 + u * T < pln) {
                         const float4 w = TW[ii[u]];
                         float v = w.x * xv[u][0];
                         v = fmaf(w.y, xv[u][1], v);
                         v = fmaf(w.z, xv[u][2], v);
                         v = fmaf(w.w, xv[u][3], v);
-                        W[(C + ii[u]) * d.kpw + kk[u]] = v * mv[u];
+                        W[kk[u] * d.wp + C + ii[u]] = v * mv[u];
                     }
                 }
             }
         }
         __syncthreads();
-        // replicate padding along i: halo rows copy the first/last plane row
-        for (int e = tid; e < nz; e += T) {
-            const float lo = W[C * d.kpw + e], hi = W[(C + nx - 1) * d.kpw + e];
-            for (int h = 0; h < C; ++h) W[h * d.kpw + e] = lo;
-            for (int h = C + nx; h < d.wrows; ++h) W[h * d.kpw + e] = hi;
+        // replicate padding along i: halo columns of every W row (warp per row)
+        for (int k = warp; k < nz; k += NW) {
+            float* wr = W + k * d.wp;
+            const float lo = wr[C], hi = wr[C + nx - 1];
+            for (int h = lane; h < wcols - nx; h += 32) {
+                if (h < C) wr[h] = lo;
+                else wr[nx + h] = hi;
+            }
         }
         __syncthreads();
 
@@ -292,36 +338,22 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
         for (int it = tid; it < nz * d.nib; it += T) {
             const int ib = it / nz, k = it - ib * nz;
             const int i0 = ib * CX;
+            const float* wr = W + k * d.wp + i0;
             float win[CX + P - 1];
 #pragma unroll
-            for (int m = 0; m < CX + P - 1; ++m) win[m] = W[(i0 + m) * d.kpw + k];
+            for (int m = 0; m < CX + P - 1; ++m) win[m] = wr[m];
             float o[CX];
-#pragma unroll
-            for (int c = 0; c < CX; ++c) o[c] = 0.f;
-#pragma unroll
-            for (int a4 = 0; a4 < PT / 4; ++a4) {
-                const float4 f4 = reinterpret_cast<const float4*>(FX)[a4];
-                const float fv[4] = {f4.x, f4.y, f4.z, f4.w};
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int a = 4 * a4 + u;
-                    if (a < P) {
-#pragma unroll
-                        for (int c = 0; c < CX; ++c) o[c] = fmaf(fv[u], win[c - a + P - 1], o[c]);
-                    }
-                }
-            }
+            fir<P, CX, -1, P - 1>(FX, win, o);
 #pragma unroll
             for (int c = 0; c < CX; ++c)
-                if (i0 + c < nx) U[(size_t)(i0 + c) * d.kpu + ZH + k] = o[c];
+                if (i0 + c < nx) U[(i0 + c) * d.kpu + ZH + k] = o[c];
         }
         __syncthreads();
         // replicate padding along k: halo columns copy the first/last column (warp per row)
         {
-            const int lane = tid & 31, warp = tid >> 5, nwarp = T >> 5;
             const int nh = d.kpu - nz;  // ZH left + the rest right
-            for (int i = warp; i < nx; i += nwarp) {
-                float* ur = U + (size_t)i * d.kpu;
+            for (int i = warp; i < nx; i += NW) {
+                float* ur = U + i * d.kpu;
                 const float lo = ur[ZH], hi = ur[ZH + nz - 1];
                 for (int h = lane; h < nh; h += 32) {
                     if (h < ZH) ur[h] = lo;
@@ -333,45 +365,21 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
 
         // k-pass into the depth-sum accumulators: lanes over i
         for (int it = tid; it < nx * d.nkb; it += T) {
-            {
-                const int kb = it / nx, i = it - kb * nx;
-                const float4* row = reinterpret_cast<const float4*>(U + (size_t)i * d.kpu + kb * CZ);
-                float win[WZ];
+            const int kb = it / nx, i = it - kb * nx;
+            float win[WZ];
+            load_window_f4<P>(U + i * d.kpu + kb * CZ, win);
+            float o[CZ];
+            fir<P, CZ, -1, C + ZH>(FZ, win, o);
 #pragma unroll
-                for (int m4 = 0; m4 < WZ / 4; ++m4) {
-                    const float4 t = row[m4];
-                    win[4 * m4] = t.x;
-                    win[4 * m4 + 1] = t.y;
-                    win[4 * m4 + 2] = t.z;
-                    win[4 * m4 + 3] = t.w;
-                }
-                float o[CZ];
-#pragma unroll
-                for (int c = 0; c < CZ; ++c) o[c] = 0.f;
-#pragma unroll
-                for (int b4 = 0; b4 < PT / 4; ++b4) {
-                    const float4 f4 = reinterpret_cast<const float4*>(FZ)[b4];
-                    const float fv[4] = {f4.x, f4.y, f4.z, f4.w};
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int b = 4 * b4 + u;
-                        if (b < P) {
-#pragma unroll
-                            for (int c = 0; c < CZ; ++c) o[c] = fmaf(fv[u], win[c - b + C + ZH], o[c]);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < CZ; ++c)
-                    if (kb * CZ + c < nz) ACC[(kb * CZ + c) * nx + i] += o[c];
-            }
+            for (int c = 0; c < CZ; ++c)
+                if (kb * CZ + c < nz) ACC[(kb * CZ + c) * nx + i] += o[c];
         }
         __syncthreads();
     }
 
     // partial depth sums of this group: part[grp][l][k][i]
-    float* pout = part + ((size_t)grp * g.nview + l) * nz * nx;
-    for (int e = tid; e < nx * nz; e += T) pout[e] = ACC[e];
+    float* pout = part + ((size_t)grp * g.nview + l) * pln;
+    for (int e = tid; e < pln; e += T) pout[e] = ACC[e];
 }
 
 // v(i,k,l) = sum over depth groups of the partials (fixed order), optionally
@@ -393,6 +401,8 @@ __global__ void k_fwd_reduce(const float* __restrict__ part, int G, size_t nproj
 
 // ============================================================================
 // Fused transpose of the blur + attenuation, separable PSF.
+//   V   nx rows x kpu: the detector plane, V[i][ZH + k], zero halo columns
+//   Zb  nz rows x wp: k-adjoint of every V row, Zb[k][C + i], zero halo columns
 // ============================================================================
 template <int P>
 __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, FusedDims d, int cls_z,
@@ -406,26 +416,26 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
     constexpr int C = S::C, CX = S::CX, CZ = S::CZ, ZH = S::ZH, WZ = S::WZ, PT = S::PT;
     extern __shared__ __align__(16) float sm[];
     const int nx = g.nx, ny = g.ny, nz = g.nz;
-    float* Zb = sm;                                 // wrows x kpw: row C+i = k-adjoint of row i, zero halo rows
-    float* V = Zb + d.warea;                        // nx x kpu: detector plane, column ZH+k, zero halo
-    float* FX = V + (size_t)nx * d.kpu;             // 3 classes x PT
-    float* FZ = FX + 3 * PT;                        // 3 classes x PT
+    float* Zb = sm;
+    float* V = Zb + d.warea;
+    float* FX = V + (size_t)nx * d.kpu;  // 3 classes x PT
+    float* FZ = FX + 3 * PT;             // 3 classes x PT
     const int tid = threadIdx.x;
-    const int T = kFusedThreads;
+    constexpr int T = kFusedThreads;
     const int grp = blockIdx.x, v = blockIdx.y, l = l0 + v;
     const int lp = g.nvp == 1 ? 0 : l;
     const int j_begin = grp * d.J, j_end = min(ny, j_begin + d.J);
     const int ox = (P - g.px) / 2, oz = (P - g.pz) / 2;
     const size_t nrow = (size_t)g.nvp * ny;
-    const size_t pln = (size_t)nx * nz;
+    const int pln = nx * nz;
 
     // stage the detector plane v(:,:,l) transposed, zero outside the detector
     for (int e = tid; e < nx * d.kpu; e += T) V[e] = 0.f;
-    for (int e = tid; e < d.wrows * d.kpw; e += T) Zb[e] = 0.f;
+    for (int e = tid; e < d.warea; e += T) Zb[e] = 0.f;
     __syncthreads();
-    for (int e = tid; e < nx * nz; e += T) {
+    for (int e = tid; e < pln; e += T) {
         const int k = e / nx, i = e - k * nx;
-        V[(size_t)i * d.kpu + ZH + k] = vin[((size_t)l * nz + k) * nx + i];
+        V[i * d.kpu + ZH + k] = vin[(size_t)l * pln + e];
     }
 
     for (int j = j_begin; j < j_end; ++j) {
@@ -438,52 +448,30 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
         }
         __syncthreads();
 
-        // k-adjoint: Zb(C+i, k) = sum_b' fz~(b') v(i, k+b'-cz), lanes over i
+        // k-adjoint: Zb[k][C+i] = sum_b' fz~(b') v(i, k+b'-cz), lanes over i
         for (int it = tid; it < nx * d.nkb; it += T) {
             const int kb = it / nx, i = it - kb * nx;
-            const float4* row = reinterpret_cast<const float4*>(V + (size_t)i * d.kpu + kb * CZ);
             float win[WZ];
-#pragma unroll
-            for (int m4 = 0; m4 < WZ / 4; ++m4) {
-                const float4 t = row[m4];
-                win[4 * m4] = t.x;
-                win[4 * m4 + 1] = t.y;
-                win[4 * m4 + 2] = t.z;
-                win[4 * m4 + 3] = t.w;
-            }
+            load_window_f4<P>(V + i * d.kpu + kb * CZ, win);
             float o[CZ];
-#pragma unroll
-            for (int c = 0; c < CZ; ++c) o[c] = 0.f;
-#pragma unroll
-            for (int b4 = 0; b4 < PT / 4; ++b4) {
-                const float4 f4 = reinterpret_cast<const float4*>(FZ)[b4];
-                const float fv[4] = {f4.x, f4.y, f4.z, f4.w};
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int b = 4 * b4 + u;
-                    if (b < P) {
-#pragma unroll
-                        for (int c = 0; c < CZ; ++c) o[c] = fmaf(fv[u], win[c + b - C + ZH], o[c]);
-                    }
-                }
-            }
+            fir<P, CZ, 1, ZH - C>(FZ, win, o);
             const int k0 = kb * CZ;
-            if (nz > 1) {  // replicate-padding folds on the first and last detector rows
+            if (nz > 1 && (k0 == 0 || k0 + CZ > nz - 1)) {  // replicate-padding folds on the first/last rows
 #pragma unroll
                 for (int c = 0; c < CZ; ++c) {
                     const int k = k0 + c;
                     if (k == 0 || k == nz - 1) {
                         const float* f = FZ + (k == 0 ? 1 : 2) * PT;
-                        float s = 0.f;
+                        float sacc = 0.f;
 #pragma unroll
-                        for (int b = 0; b < P; ++b) s = fmaf(f[b], win[c + b - C + ZH], s);
-                        o[c] = s;
+                        for (int b = 0; b < P; ++b) sacc = fmaf(f[b], win[c + b - C + ZH], sacc);
+                        o[c] = sacc;
                     }
                 }
             }
 #pragma unroll
             for (int c = 0; c < CZ; ++c)
-                if (k0 + c < nz) Zb[(size_t)(C + i) * d.kpw + k0 + c] = o[c];
+                if (k0 + c < nz) Zb[(k0 + c) * d.wp + C + i] = o[c];
         }
         __syncthreads();
 
@@ -495,103 +483,100 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
             const int i0 = ib * CX;
             float mbv[CX];
 #pragma unroll
-            for (int c = 0; c < CX; ++c) mbv[c] = (i0 + c < nx) ? __ldg(mb + (size_t)(i0 + c) * nz + k) : 0.f;
+            for (int c = 0; c < CX; ++c) mbv[c] = (i0 + c < nx) ? __ldg(mb + (i0 + c) * nz + k) : 0.f;
+            const float* zr = Zb + k * d.wp + i0;
             float win[CX + P - 1];
 #pragma unroll
-            for (int m = 0; m < CX + P - 1; ++m) win[m] = Zb[(i0 + m) * d.kpw + k];
+            for (int m = 0; m < CX + P - 1; ++m) win[m] = zr[m];
             float o[CX];
+            fir<P, CX, 1, 0>(FX, win, o);
+            if (i0 == 0 || i0 + CX > nx - 1) {
 #pragma unroll
-            for (int c = 0; c < CX; ++c) o[c] = 0.f;
+                for (int c = 0; c < CX; ++c) {
+                    const int i = i0 + c;
+                    if (i == 0 || i == nx - 1) {
+                        const float* f = FX + (i == 0 ? 1 : 2) * PT;
+                        float sacc = 0.f;
 #pragma unroll
-            for (int a4 = 0; a4 < PT / 4; ++a4) {
-                const float4 f4 = reinterpret_cast<const float4*>(FX)[a4];
-                const float fv[4] = {f4.x, f4.y, f4.z, f4.w};
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int a = 4 * a4 + u;
-                    if (a < P) {
-#pragma unroll
-                        for (int c = 0; c < CX; ++c) o[c] = fmaf(fv[u], win[c + a], o[c]);
+                        for (int a = 0; a < P; ++a) sacc = fmaf(f[a], win[c + a], sacc);
+                        o[c] = sacc;
                     }
                 }
             }
 #pragma unroll
-            for (int c = 0; c < CX; ++c) {
-                const int i = i0 + c;
-                if (i == 0 || i == nx - 1) {
-                    const float* f = FX + (i == 0 ? 1 : 2) * PT;
-                    float s = 0.f;
-#pragma unroll
-                    for (int a = 0; a < P; ++a) s = fmaf(f[a], win[c + a], s);
-                    o[c] = s;
-                }
-                if (i < nx) tout[(size_t)i * nz + k] = o[c] * mbv[c];
-            }
+            for (int c = 0; c < CX; ++c)
+                if (i0 + c < nx) tout[(i0 + c) * nz + k] = o[c] * mbv[c];
         }
         __syncthreads();
     }
 }
 
-// x_t(q,k) (+)= sum_{v in chunk} sum_{e < MAXE} w_e t[v][p_e][k]  (lanes over k)
+// x_t(q,k) (+)= sum_{v in chunk} sum_{e < MAXE} w_e t[v][p_e][k]
 // with the MLEM update x <- x e / s on the last chunk when em_x is set.  The
 // lists are laid out [q][l][e] so one destination's entries for all views are
 // contiguous; each entry holds the premultiplied offset p*nz of its source
-// column.  Per view the few terms are summed plainly, the views with Kahan.
-template <int MAXE>
+// column.  A thread owns VEC consecutive k of one destination (float4 loads
+// when nz % 4 == 0).  Per view the few terms are summed plainly, the views
+// with Kahan compensation.
+template <int VEC>
+struct VecT;
+template <>
+struct VecT<1> {
+    using type = float;
+};
+template <>
+struct VecT<4> {
+    using type = float4;
+};
+
+template <int MAXE, int VEC>
 __global__ void __launch_bounds__(256) k_adj_rot_t(Geometry g, const AdjEntry* __restrict__ adj,
                                                    const float* __restrict__ slab, int l0, int nv, float* out,
                                                    int accumulate, float* em_x, const float* __restrict__ em_s)
 {
+    using VT = typename VecT<VEC>::type;
     const int nxy = g.nx * g.ny;
+    const int nzv = g.nz / VEC;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nxy * g.nz) return;
-    const int q = idx / g.nz;
-    const int k = idx - q * g.nz;
+    if (idx >= nxy * nzv) return;
+    const int q = idx / nzv;
+    const int k = (idx - q * nzv) * VEC;
     const AdjEntry* e = adj + ((size_t)q * g.nview + l0) * MAXE;
     const float* t = slab + k;
     const size_t vstride = (size_t)nxy * g.nz;
-    KSum acc;
-    int v = 0;
-    for (; v + 1 < nv; v += 2) {
-        AdjEntry a0[MAXE], a1[MAXE];
+    KSum acc[VEC];
+    for (int v = 0; v < nv; ++v) {
+        AdjEntry a[MAXE];
+#pragma unroll
+        for (int m = 0; m < MAXE; ++m) a[m] = e[m];
+        VT tv[MAXE];
+#pragma unroll
+        for (int m = 0; m < MAXE; ++m) tv[m] = *reinterpret_cast<const VT*>(t + a[m].p);
+        float sv[VEC];
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) sv[u] = 0.f;
 #pragma unroll
         for (int m = 0; m < MAXE; ++m) {
-            a0[m] = e[m];
-            a1[m] = e[MAXE + m];
-        }
-        float t0[MAXE], t1[MAXE];
+            const float* tf = reinterpret_cast<const float*>(&tv[m]);
 #pragma unroll
-        for (int m = 0; m < MAXE; ++m) {
-            t0[m] = __ldg(t + a0[m].p);
-            t1[m] = __ldg(t + vstride + a1[m].p);
+            for (int u = 0; u < VEC; ++u) sv[u] = fmaf(a[m].w, tf[u], sv[u]);
         }
-        float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-        for (int m = 0; m < MAXE; ++m) {
-            s0 = fmaf(a0[m].w, t0[m], s0);
-            s1 = fmaf(a1[m].w, t1[m], s1);
-        }
-        acc.add(s0);
-        acc.add(s1);
-        e += 2 * MAXE;
-        t += 2 * vstride;
+        for (int u = 0; u < VEC; ++u) acc[u].add(sv[u]);
+        e += MAXE;
+        t += vstride;
     }
-    if (v < nv) {
-        float s0 = 0.f;
+    const size_t o = (size_t)q * g.nz + k;
 #pragma unroll
-        for (int m = 0; m < MAXE; ++m) {
-            const AdjEntry a = e[m];
-            s0 = fmaf(a.w, __ldg(t + a.p), s0);
+    for (int u = 0; u < VEC; ++u) {
+        float val = acc[u].value();
+        if (accumulate) val += out[o + u];
+        if (em_x) {
+            const float sv = em_s[o + u];
+            em_x[o + u] = sv > 0.f ? (em_x[o + u] * val) / sv : 0.f;
+        } else {
+            out[o + u] = val;
         }
-        acc.add(s0);
-    }
-    float val = acc.value();
-    if (accumulate) val += out[idx];
-    if (em_x) {
-        const float sv = em_s[idx];
-        em_x[idx] = sv > 0.f ? (em_x[idx] * val) / sv : 0.f;
-    } else {
-        out[idx] = val;
     }
 }
 
@@ -608,9 +593,8 @@ FusedDims dims_for(const Geometry& g, int J)
     FusedDims d;
     d.nib = (g.nx + S::CX - 1) / S::CX;
     d.nkb = (g.nz + S::CZ - 1) / S::CZ;
-    d.wrows = d.nib * S::CX + 2 * S::C;
-    d.kpw = g.nz | 1;
-    d.warea = (d.wrows * d.kpw + 3) & ~3;
+    d.wp = (d.nib * S::CX + 2 * S::C) | 1;
+    d.warea = (g.nz * d.wp + 3) & ~3;
     int kpu = d.nkb * S::CZ + 2 * S::ZH;
     kpu = (kpu + 3) & ~3;
     if (((kpu / 4) & 1) == 0) kpu += 4;
@@ -719,12 +703,16 @@ cudaError_t launch_fwd_reduce(const spect_plan_s& P, float* v, const float* em_y
 cudaError_t launch_adj_rot_t(const spect_plan_s& P, int l0, int nv, float* out, int accumulate, float* em_x,
                              const float* em_s, cudaStream_t st)
 {
-    const size_t n = (size_t)P.g.nx * P.g.ny * P.g.nz;
+    const bool vec4 = (P.g.nz % 4) == 0;
+    const size_t n = (size_t)P.g.nx * P.g.ny * (vec4 ? P.g.nz / 4 : P.g.nz);
     const unsigned blocks = (unsigned)((n + 255) / 256);
     switch (P.adj_max) {
-#define SPECT_ADJ(M)                                                                                             \
-    case M:                                                                                                      \
-        k_adj_rot_t<M><<<blocks, 256, 0, st>>>(P.g, P.adjf, P.slab, l0, nv, out, accumulate, em_x, em_s); \
+#define SPECT_ADJ(M)                                                                                                 \
+    case M:                                                                                                          \
+        if (vec4)                                                                                                    \
+            k_adj_rot_t<M, 4><<<blocks, 256, 0, st>>>(P.g, P.adjf, P.slab, l0, nv, out, accumulate, em_x, em_s); \
+        else                                                                                                         \
+            k_adj_rot_t<M, 1><<<blocks, 256, 0, st>>>(P.g, P.adjf, P.slab, l0, nv, out, accumulate, em_x, em_s); \
         break;
         SPECT_ADJ(1) SPECT_ADJ(2) SPECT_ADJ(3) SPECT_ADJ(4) SPECT_ADJ(5) SPECT_ADJ(6) SPECT_ADJ(7) SPECT_ADJ(8)
 #undef SPECT_ADJ
