@@ -198,6 +198,7 @@ def run_ours(args):
         total_ms = timed_steps(args.steps)
         wall = time.perf_counter() - t0
     launches = plan.profile_read(reset=True)
+    plan.check()
     if dist:
         t = torch.tensor([total_ms], device=device)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)

@@ -207,6 +207,15 @@ spect_status spect_profile_enable(spect_plan plan, int enable);
  */
 spect_status spect_profile_read(spect_plan plan, long long* launches, double* ms, int reset);
 
+/*
+ * spect_plan_check -- synchronise the device and report whether any kernel
+ * of the plan gave up a bounded wait since the last check: SPECT_ETIMEOUT if
+ * one did (the outputs of the affected calls are not valid), else SPECT_OK.
+ * The plan's error word is cleared.  The fused kernels wait on their own
+ * bulk copies with a limit of about one second instead of blocking forever.
+ */
+spect_status spect_plan_check(spect_plan plan);
+
 /* spect_plan_destroy -- release the plan; NULL is accepted and returns OK.
  * Waits for the plan's outstanding work on the device before freeing. */
 spect_status spect_plan_destroy(spect_plan plan);

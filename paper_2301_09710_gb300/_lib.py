@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH):
         lib.spect_profile_read.restype = st
         lib.spect_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
         lib.spect_fp32_peak.restype = st
+        lib.spect_plan_check.argtypes = [vp]
+        lib.spect_plan_check.restype = st
         lib.spect_plan_destroy.argtypes = [vp]
         lib.spect_plan_destroy.restype = st
         lib.spect_last_error.argtypes = []

@@ -79,8 +79,9 @@ cudaError_t launch_transpose(const float* in, float* out, int R, int C, cudaStre
 
 // mubar[l][j][i][k] = exp(-dy (mu~(j)/2 + sum_{s>j} mu~(s))), Eq. (1), for every
 // view; one thread per (l, i, k) walking j from the detector side.  mu_t is mu
-// in the [j][i][k] layout.
-__global__ void k_mubar_cache(Geometry g, const ViewRot* __restrict__ rot, const float* __restrict__ mu_t,
+// in the [j][i][k] layout; planes (l, j) are ps floats apart (16-byte aligned
+// for bulk copies).
+__global__ void k_mubar_cache(Geometry g, int ps, const ViewRot* __restrict__ rot, const float* __restrict__ mu_t,
                               float* __restrict__ mubar)
 {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -102,22 +103,22 @@ __global__ void k_mubar_cache(Geometry g, const ViewRot* __restrict__ rot, const
         mv = __fmaf_rn(w.y, m[g.nz], mv);
         mv = __fmaf_rn(w.z, m[rs], mv);
         mv = __fmaf_rn(w.w, m[rs + g.nz], mv);
-        mubar[(((size_t)l * g.ny + j) * g.nx + i) * g.nz + k] = g.has_mu ? sc.step(mv, g.dy) : 1.f;
+        mubar[((size_t)l * g.ny + j) * ps + (size_t)i * g.nz + k] = g.has_mu ? sc.step(mv, g.dy) : 1.f;
     }
 }
 
 cudaError_t launch_mubar_cache(const spect_plan_s& P, const float* mu_t, cudaStream_t st)
 {
     const size_t n = (size_t)P.g.nx * P.g.nz * P.g.nview;
-    k_mubar_cache<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.g, P.rot, mu_t, P.mubar);
+    k_mubar_cache<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.g, P.ps, P.rot, mu_t, P.mubar);
     return cudaGetLastError();
 }
 
 // Fixed-length adjacency lists for the transposed rotation: for destination
-// q and view l, up to `maxe` (source column offset p*nz, weight) pairs,
+// q and view l, up to `maxe` (source column offset j*ps + i*nz, weight) pairs,
 // zero-padded, laid out [q][l][e].  The candidate search and weights are those
 // of k_build_adjacency (rotate.cu).
-__global__ void k_build_adjacency_fixed(Geometry g, const ViewRot* __restrict__ rot, int maxe, AdjEntry* adj)
+__global__ void k_build_adjacency_fixed(Geometry g, int ps, const ViewRot* __restrict__ rot, int maxe, AdjEntry* adj)
 {
     const size_t nxy = (size_t)g.nx * g.ny;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -144,7 +145,7 @@ __global__ void k_build_adjacency_fixed(Geometry g, const ViewRot* __restrict__ 
             const float w = bilinear_w(s, di, dj);
             if (w == 0.f || cnt >= maxe) continue;
             AdjEntry e;
-            e.p = (pi + g.nx * pj) * g.nz;  // offset of the source column in a [j][i][k] slab
+            e.p = pj * ps + pi * g.nz;  // offset of the source column in a [j][i][k] slab with plane stride ps
             e.w = w;
             out[cnt++] = e;
         }
@@ -159,7 +160,7 @@ __global__ void k_build_adjacency_fixed(Geometry g, const ViewRot* __restrict__ 
 cudaError_t launch_build_adjacency_fixed(const spect_plan_s& P, cudaStream_t st)
 {
     const size_t n = (size_t)P.g.nx * P.g.ny * P.g.nview;
-    k_build_adjacency_fixed<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.g, P.rot, P.adj_max, P.adjf);
+    k_build_adjacency_fixed<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.g, P.ps, P.rot, P.adj_max, P.adjf);
     return cudaGetLastError();
 }
 
@@ -174,7 +175,12 @@ cudaError_t launch_build_adjacency_fixed(const spect_plan_s& P, cudaStream_t st)
 //   U   nx rows x kpu: i-pass output, U[i][ZH + k], with replicate halo
 //       columns; kpu/4 is odd so the k-pass float4 windows (lanes over i) are
 //       bank-conflict free.
+//   MB  the attenuation plane mubar(:, j, :) of the current depth, brought in
+//       by one TMA bulk copy issued a plane ahead.
+//   taps and rotation table of the current and the next plane (double buffer),
 //   ACC nz x nx depth-sum accumulators of the group, [k][i].
+// Per plane there are three block barriers: after the rotation, after the
+// i-pass, after the k-pass (which also prepares the next plane's table/taps).
 // ============================================================================
 template <int P>
 struct Sep {
@@ -195,12 +201,19 @@ struct FusedDims {
     int kpu;    // U row pitch (>= nkb*CZ + 2*ZH, multiple of 4, pitch/4 odd)
     int nib, nkb;
     int J, G;   // depth planes per block, depth groups
+    int ps;     // plane stride of the attenuation cache / slab (nx*nz rounded up to 4)
 };
 
-__host__ __device__ inline size_t fused_smem_floats(const FusedDims& d, int nx, int nz, int PT)
+__host__ __device__ inline size_t fwd_smem_floats(const FusedDims& d, int nx, int nz, int PT)
 {
-    // W | U | taps (6 PT) | rotation table (5 nx) | depth-sum accumulators (nx*nz, forward only)
-    return (size_t)d.warea + (size_t)nx * d.kpu + 6 * (size_t)PT + 5 * (size_t)nx + (size_t)nx * nz;
+    // W | U | MB | taps 2x(FX,FZ) | table 2x(TW,TB) | ACC | mbarrier
+    return (size_t)d.warea + (size_t)nx * d.kpu + d.ps + 4 * (size_t)PT + 10 * (size_t)nx + (size_t)nx * nz + 4;
+}
+
+__host__ __device__ inline size_t adj_smem_floats(const FusedDims& d, int nx, int PT)
+{
+    // Zb | V | MB x2 | taps 2x(FX[3],FZ[3]) | 2 mbarriers
+    return (size_t)d.warea + (size_t)nx * d.kpu + 2 * (size_t)d.ps + 12 * (size_t)PT + 8;
 }
 
 template <int P>
@@ -239,6 +252,12 @@ __device__ __forceinline__ void fir(const float* taps, const float (&win)[WN], f
     }
 }
 
+// Record a timed-out bounded wait in the plan's error word.
+__device__ __forceinline__ void flag_timeout(int* err)
+{
+    if (err) atomicExch(err, (int)SPECT_ETIMEOUT);
+}
+
 template <int P>
 __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, FusedDims d,
                                                                      const ViewRot* __restrict__ rot,
@@ -246,7 +265,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
                                                                      const float* __restrict__ mubar,
                                                                      const float* __restrict__ fx,
                                                                      const float* __restrict__ fz,
-                                                                     float* __restrict__ part, int l0)
+                                                                     float* __restrict__ part, int l0, int* err)
 {
     using S = Sep<P>;
     constexpr int C = S::C, CX = S::CX, CZ = S::CZ, ZH = S::ZH, WZ = S::WZ, PT = S::PT;
@@ -254,13 +273,14 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     float* W = sm;
     float* U = W + d.warea;
-    float* FX = U + (size_t)nx * d.kpu;
-    float* FZ = FX + PT;
-    float4* TW = reinterpret_cast<float4*>(FZ + PT);
-    int* TB = reinterpret_cast<int*>(TW + nx);
-    float* ACC = reinterpret_cast<float*>(TB + nx);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int T = kFusedThreads, NW = kFusedThreads / 32;
+    float* MB = U + (size_t)nx * d.kpu;
+    float* TAP = MB + d.ps;                            // [2][FX PT | FZ PT]
+    float4* TW = reinterpret_cast<float4*>(TAP + 4 * PT);  // [2][nx]
+    int* TB = reinterpret_cast<int*>(TW + 2 * nx);         // [2][nx]
+    float* ACC = reinterpret_cast<float*>(TB + 2 * nx);    // nz x nx, [k][i]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(ACC + (((size_t)nx * nz + 1) & ~(size_t)1));
+    const int tid = threadIdx.x, lane = tid & 31;
+    constexpr int T = kFusedThreads;
     const int grp = blockIdx.x, l = l0 + blockIdx.y;
     const int lp = g.nvp == 1 ? 0 : l;
     const int j_begin = grp * d.J, j_end = min(ny, j_begin + d.J);
@@ -268,27 +288,45 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
     const int ox = (P - g.px) / 2, oz = (P - g.pz) / 2;  // zero-padding offsets of the taps
     const int pln = nx * nz;
     const int wcols = d.nib * CX + 2 * C;  // used W columns
+    const float* mub = mubar + ((size_t)l * ny) * d.ps;
 
-    for (int e = tid; e < nx * nz; e += T) ACC[e] = 0.f;
-
-    for (int j = j_begin; j < j_end; ++j) {
-        // taps (zero-padded to P, centred) and the rotation table of row j
+    // taps (zero-padded to P, centred) and rotation table of plane j into buffer b
+    auto prepare = [&](int j, int b) {
+        float* FX = TAP + b * 2 * PT;
         for (int a = tid; a < PT; a += T) {
             const int ax = a - ox, az = a - oz;
-            FX[a] = (ax >= 0 && ax < g.px) ? fx[((size_t)lp * ny + j) * g.px + ax] : 0.f;
-            FZ[a] = (az >= 0 && az < g.pz) ? fz[((size_t)lp * ny + j) * g.pz + az] : 0.f;
+            FX[a] = (ax >= 0 && ax < g.px) ? __ldg(fx + ((size_t)lp * ny + j) * g.px + ax) : 0.f;
+            FX[PT + a] = (az >= 0 && az < g.pz) ? __ldg(fz + ((size_t)lp * ny + j) * g.pz + az) : 0.f;
         }
-        for (int i = tid; i < nx; i += T) rot_table_entry(i, j, r, g, TW[i], TB[i]);
-        __syncthreads();
+        for (int i = tid; i < nx; i += T) rot_table_entry(i, j, r, g, TW[b * nx + i], TB[b * nx + i]);
+    };
+
+    for (int e = tid; e < pln; e += T) ACC[e] = 0.f;
+    prepare(j_begin, 0);
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tma_load_1d(MB, mub + (size_t)j_begin * d.ps, (unsigned)d.ps * 4u, bar);
+    }
+    __syncthreads();
+
+    unsigned phase = 0;
+    for (int j = j_begin; j < j_end; ++j) {
+        const int b = (j - j_begin) & 1;
+        const float* FX = TAP + b * 2 * PT;
+        const float* FZ = FX + PT;
+        const float4* tw = TW + b * nx;
+        const int* tb = TB + b * nx;
 
         // rotate + attenuate the plane into W[k][C+i]; four points per thread
-        // per batch keep 20 independent loads in flight
-        {
-            const float* mb = mubar + ((size_t)l * ny + j) * pln;
+        // per batch keep 16 independent gathers in flight
+        const bool ok = mbar_wait_bounded(bar, phase);
+        phase ^= 1u;
+        if (ok) {
             const int sdi = T / nz, sdk = T - sdi * nz;  // (i,k) step of one stride T
             int ci = tid / nz, ck = tid - ci * nz;
             for (int f0 = tid; f0 < pln; f0 += 4 * T) {
-                float xv[4][4], mv[4];
+                float xv[4][4];
                 int ii[4], kk[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -301,69 +339,94 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
                         ++ci;
                     }
                     if (f0 + u * T < pln) {
-                        const float* xb = xt + (TB[ii[u]] * nz + kk[u]);
+                        const float* xb = xt + (tb[ii[u]] * nz + kk[u]);
                         xv[u][0] = __ldg(xb);
                         xv[u][1] = __ldg(xb + nz);
                         xv[u][2] = __ldg(xb + pln);
                         xv[u][3] = __ldg(xb + pln + nz);
-                        mv[u] = __ldg(mb + f0 + u * T);
                     }
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     if (f0 + u * T < pln) {
-                        const float4 w = TW[ii[u]];
+                        const float4 w = tw[ii[u]];
                         float v = w.x * xv[u][0];
                         v = fmaf(w.y, xv[u][1], v);
                         v = fmaf(w.z, xv[u][2], v);
                         v = fmaf(w.w, xv[u][3], v);
-                        W[kk[u] * d.wp + C + ii[u]] = v * mv[u];
+                        v *= MB[f0 + u * T];
+                        float* wr = W + kk[u] * d.wp;
+                        wr[C + ii[u]] = v;
+                        if (ii[u] == 0)  // replicate padding along i: left halo columns
+                            for (int h = 0; h < C; ++h) wr[h] = v;
+                        if (ii[u] == nx - 1)  // right halo columns
+                            for (int h = C + nx; h < wcols; ++h) wr[h] = v;
                     }
                 }
             }
         }
-        __syncthreads();
-        // replicate padding along i: halo columns of every W row (warp per row)
-        for (int k = warp; k < nz; k += NW) {
-            float* wr = W + k * d.wp;
-            const float lo = wr[C], hi = wr[C + nx - 1];
-            for (int h = lane; h < wcols - nx; h += 32) {
-                if (h < C) wr[h] = lo;
-                else wr[nx + h] = hi;
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                flag_timeout(err);
+                mbar_wait_bounded(bar, phase ^ 1u);  // give the copy in flight a last chance to land
             }
+            return;
         }
-        __syncthreads();
+        // MB is free again: bring in the next plane's attenuation
+        if (tid == 0 && j + 1 < j_end) {
+            fence_proxy_async_smem();
+            tma_load_1d(MB, mub + (size_t)(j + 1) * d.ps, (unsigned)d.ps * 4u, bar);
+        }
 
-        // i-pass: U(i,k) = sum_a fx(a) w(clamp(i-a+cx), k); lanes over k
-        for (int it = tid; it < nz * d.nib; it += T) {
-            const int ib = it / nz, k = it - ib * nz;
+        // i-pass: U(i,k) = sum_a fx(a) w(clamp(i-a+cx), k); lanes over k.  The
+        // replicate halo columns of U are written by the warp holding k = 0 or
+        // k = nz-1, one lane per column, from shuffled values.
+        const int nxi = nz * d.nib;
+        for (int base = 0; base < nxi; base += T) {
+            const int it = base + tid;
+            const bool valid = it < nxi;
+            const int ib = valid ? it / nz : 0, k = valid ? it - ib * nz : 0;
             const int i0 = ib * CX;
-            const float* wr = W + k * d.wp + i0;
-            float win[CX + P - 1];
-#pragma unroll
-            for (int m = 0; m < CX + P - 1; ++m) win[m] = wr[m];
             float o[CX];
-            fir<P, CX, -1, P - 1>(FX, win, o);
+            if (valid) {
+                const float* wr = W + k * d.wp + i0;
+                float win[CX + P - 1];
 #pragma unroll
-            for (int c = 0; c < CX; ++c)
-                if (i0 + c < nx) U[(i0 + c) * d.kpu + ZH + k] = o[c];
-        }
-        __syncthreads();
-        // replicate padding along k: halo columns copy the first/last column (warp per row)
-        {
-            const int nh = d.kpu - nz;  // ZH left + the rest right
-            for (int i = warp; i < nx; i += NW) {
-                float* ur = U + i * d.kpu;
-                const float lo = ur[ZH], hi = ur[ZH + nz - 1];
-                for (int h = lane; h < nh; h += 32) {
-                    if (h < ZH) ur[h] = lo;
-                    else ur[nz + h] = hi;
+                for (int m = 0; m < CX + P - 1; ++m) win[m] = wr[m];
+                fir<P, CX, -1, P - 1>(FX, win, o);
+#pragma unroll
+                for (int c = 0; c < CX; ++c)
+                    if (i0 + c < nx) U[(i0 + c) * d.kpu + ZH + k] = o[c];
+            }
+            const unsigned m0 = __ballot_sync(0xffffffffu, valid && k == 0);
+            const unsigned m1 = __ballot_sync(0xffffffffu, valid && k == nz - 1);
+            if (m0) {
+                const int src = __ffs(m0) - 1;
+                const int i0s = __shfl_sync(0xffffffffu, i0, src);
+#pragma unroll
+                for (int c = 0; c < CX; ++c) {
+                    const float vv = __shfl_sync(0xffffffffu, o[c], src);
+                    if (i0s + c < nx)
+                        for (int h = lane; h < ZH; h += 32) U[(i0s + c) * d.kpu + h] = vv;
+                }
+            }
+            if (m1) {
+                const int src = __ffs(m1) - 1;
+                const int i0s = __shfl_sync(0xffffffffu, i0, src);
+                const int nr = d.kpu - ZH - nz;
+#pragma unroll
+                for (int c = 0; c < CX; ++c) {
+                    const float vv = __shfl_sync(0xffffffffu, o[c], src);
+                    if (i0s + c < nx)
+                        for (int h = lane; h < nr; h += 32) U[(i0s + c) * d.kpu + ZH + nz + h] = vv;
                 }
             }
         }
         __syncthreads();
 
-        // k-pass into the depth-sum accumulators: lanes over i
+        // next plane's taps and table (other buffer), then the k-pass into the
+        // depth-sum accumulators: lanes over i
+        if (j + 1 < j_end) prepare(j + 1, b ^ 1);
         for (int it = tid; it < nx * d.nkb; it += T) {
             const int kb = it / nx, i = it - kb * nx;
             float win[WZ];
@@ -403,6 +466,9 @@ __global__ void k_fwd_reduce(const float* __restrict__ part, int G, size_t nproj
 // Fused transpose of the blur + attenuation, separable PSF.
 //   V   nx rows x kpu: the detector plane, V[i][ZH + k], zero halo columns
 //   Zb  nz rows x wp: k-adjoint of every V row, Zb[k][C + i], zero halo columns
+//   MB  two plane buffers: each receives mubar(:, j, :) by TMA, is overwritten
+//       in place with t = wbar * mubar, and leaves for the slab by a TMA bulk
+//       store; the buffer of plane j+1 is loaded while plane j is computed.
 // ============================================================================
 template <int P>
 __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, FusedDims d, int cls_z,
@@ -410,7 +476,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
                                                                      const float* __restrict__ mubar,
                                                                      const float* __restrict__ fx_adj,
                                                                      const float* __restrict__ fz_adj,
-                                                                     float* __restrict__ slab, int l0)
+                                                                     float* __restrict__ slab, int l0, int* err)
 {
     using S = Sep<P>;
     constexpr int C = S::C, CX = S::CX, CZ = S::CZ, ZH = S::ZH, WZ = S::WZ, PT = S::PT;
@@ -418,8 +484,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     float* Zb = sm;
     float* V = Zb + d.warea;
-    float* FX = V + (size_t)nx * d.kpu;  // 3 classes x PT
-    float* FZ = FX + 3 * PT;             // 3 classes x PT
+    float* MB = V + (size_t)nx * d.kpu;  // [2][ps]
+    float* TAP = MB + 2 * (size_t)d.ps;  // [2][FX 3 classes | FZ 3 classes] x PT
+    uint64_t* bar = reinterpret_cast<uint64_t*>(TAP + 12 * PT);
     const int tid = threadIdx.x;
     constexpr int T = kFusedThreads;
     const int grp = blockIdx.x, v = blockIdx.y, l = l0 + v;
@@ -428,25 +495,50 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
     const int ox = (P - g.px) / 2, oz = (P - g.pz) / 2;
     const size_t nrow = (size_t)g.nvp * ny;
     const int pln = nx * nz;
+    const float* mub = mubar + ((size_t)l * ny) * d.ps;
+    float* tsl = slab + ((size_t)v * ny) * d.ps;
+
+    auto prepare = [&](int j, int b) {
+        float* F = TAP + b * 6 * PT;
+        for (int e = tid; e < 3 * PT; e += T) {
+            const int c = e / PT, a = e - c * PT;
+            const int ax = a - ox, az = a - oz;
+            F[e] = (ax >= 0 && ax < g.px) ? __ldg(fx_adj + ((size_t)c * nrow + (size_t)lp * ny + j) * g.px + ax) : 0.f;
+            F[3 * PT + e] = (c < cls_z && az >= 0 && az < g.pz)
+                                ? __ldg(fz_adj + ((size_t)c * nrow + (size_t)lp * ny + j) * g.pz + az)
+                                : 0.f;
+        }
+    };
 
     // stage the detector plane v(:,:,l) transposed, zero outside the detector
     for (int e = tid; e < nx * d.kpu; e += T) V[e] = 0.f;
     for (int e = tid; e < d.warea; e += T) Zb[e] = 0.f;
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tma_load_1d(MB, mub + (size_t)j_begin * d.ps, (unsigned)d.ps * 4u, bar);
+    }
+    prepare(j_begin, 0);
     __syncthreads();
     for (int e = tid; e < pln; e += T) {
         const int k = e / nx, i = e - k * nx;
         V[i * d.kpu + ZH + k] = vin[(size_t)l * pln + e];
     }
+    __syncthreads();
 
+    unsigned phase[2] = {0u, 0u};
     for (int j = j_begin; j < j_end; ++j) {
-        for (int e = tid; e < 3 * PT; e += T) {
-            const int c = e / PT, a = e - c * PT;
-            const int ax = a - ox, az = a - oz;
-            FX[e] = (ax >= 0 && ax < g.px) ? fx_adj[((size_t)c * nrow + (size_t)lp * ny + j) * g.px + ax] : 0.f;
-            FZ[e] = (c < cls_z && az >= 0 && az < g.pz) ? fz_adj[((size_t)c * nrow + (size_t)lp * ny + j) * g.pz + az]
-                                                       : 0.f;
+        const int n = j - j_begin, b = n & 1;
+        const float* FX = TAP + b * 6 * PT;
+        const float* FZ = FX + 3 * PT;
+        // the other buffer: once the previous plane's bulk store has read it,
+        // it receives the next plane's attenuation
+        if (tid == 0 && j + 1 < j_end) {
+            tma_store_wait_read<0>();
+            tma_load_1d(MB + (b ^ 1) * (size_t)d.ps, mub + (size_t)(j + 1) * d.ps, (unsigned)d.ps * 4u, bar + (b ^ 1));
         }
-        __syncthreads();
+        if (j + 1 < j_end) prepare(j + 1, b ^ 1);
 
         // k-adjoint: Zb[k][C+i] = sum_b' fz~(b') v(i, k+b'-cz), lanes over i
         for (int it = tid; it < nx * d.nkb; it += T) {
@@ -464,7 +556,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
                         const float* f = FZ + (k == 0 ? 1 : 2) * PT;
                         float sacc = 0.f;
 #pragma unroll
-                        for (int b = 0; b < P; ++b) sacc = fmaf(f[b], win[c + b - C + ZH], sacc);
+                        for (int bb = 0; bb < P; ++bb) sacc = fmaf(f[bb], win[c + bb - C + ZH], sacc);
                         o[c] = sacc;
                     }
                 }
@@ -475,47 +567,63 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
         }
         __syncthreads();
 
-        // i-adjoint times mubar -> t slab [v][j][i][k]; lanes over k
-        const float* mb = mubar + ((size_t)l * ny + j) * pln;
-        float* tout = slab + ((size_t)v * ny + j) * pln;
-        for (int it = tid; it < nz * d.nib; it += T) {
-            const int ib = it / nz, k = it - ib * nz;
-            const int i0 = ib * CX;
-            float mbv[CX];
+        // i-adjoint times mubar, in place in MB[b]; lanes over k
+        float* mb = MB + b * (size_t)d.ps;
+        const bool ok = mbar_wait_bounded(bar + b, phase[b]);
+        phase[b] ^= 1u;
+        if (ok) {
+            for (int it = tid; it < nz * d.nib; it += T) {
+                const int ib = it / nz, k = it - ib * nz;
+                const int i0 = ib * CX;
+                const float* zr = Zb + k * d.wp + i0;
+                float win[CX + P - 1];
 #pragma unroll
-            for (int c = 0; c < CX; ++c) mbv[c] = (i0 + c < nx) ? __ldg(mb + (i0 + c) * nz + k) : 0.f;
-            const float* zr = Zb + k * d.wp + i0;
-            float win[CX + P - 1];
+                for (int m = 0; m < CX + P - 1; ++m) win[m] = zr[m];
+                float o[CX];
+                fir<P, CX, 1, 0>(FX, win, o);
+                if (i0 == 0 || i0 + CX > nx - 1) {
 #pragma unroll
-            for (int m = 0; m < CX + P - 1; ++m) win[m] = zr[m];
-            float o[CX];
-            fir<P, CX, 1, 0>(FX, win, o);
-            if (i0 == 0 || i0 + CX > nx - 1) {
+                    for (int c = 0; c < CX; ++c) {
+                        const int i = i0 + c;
+                        if (i == 0 || i == nx - 1) {
+                            const float* f = FX + (i == 0 ? 1 : 2) * PT;
+                            float sacc = 0.f;
 #pragma unroll
-                for (int c = 0; c < CX; ++c) {
-                    const int i = i0 + c;
-                    if (i == 0 || i == nx - 1) {
-                        const float* f = FX + (i == 0 ? 1 : 2) * PT;
-                        float sacc = 0.f;
-#pragma unroll
-                        for (int a = 0; a < P; ++a) sacc = fmaf(f[a], win[c + a], sacc);
-                        o[c] = sacc;
+                            for (int a = 0; a < P; ++a) sacc = fmaf(f[a], win[c + a], sacc);
+                            o[c] = sacc;
+                        }
                     }
                 }
-            }
 #pragma unroll
-            for (int c = 0; c < CX; ++c)
-                if (i0 + c < nx) tout[(i0 + c) * nz + k] = o[c] * mbv[c];
+                for (int c = 0; c < CX; ++c)
+                    if (i0 + c < nx) {
+                        float* mp = mb + (i0 + c) * nz + k;
+                        *mp = o[c] * *mp;
+                    }
+            }
         }
-        __syncthreads();
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                flag_timeout(err);
+                mbar_wait_bounded(bar + b, phase[b] ^ 1u);
+                tma_store_wait_all();
+            }
+            return;
+        }
+        // t plane -> slab[v][j]
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            tma_store_1d(tsl + (size_t)j * d.ps, mb, (unsigned)d.ps * 4u);
+        }
     }
+    if (tid == 0) tma_store_wait_all();
 }
 
 // x_t(q,k) (+)= sum_{v in chunk} sum_{e < MAXE} w_e t[v][p_e][k]
 // with the MLEM update x <- x e / s on the last chunk when em_x is set.  The
 // lists are laid out [q][l][e] so one destination's entries for all views are
 // contiguous; each entry holds the premultiplied offset p*nz of its source
-// column.  A thread owns VEC consecutive k of one destination (float4 loads
+// column in the slab.  A thread owns VEC consecutive k of one destination (float4 loads
 // when nz % 4 == 0).  Per view the few terms are summed plainly, the views
 // with Kahan compensation.
 template <int VEC>
@@ -530,7 +638,7 @@ struct VecT<4> {
 };
 
 template <int MAXE, int VEC>
-__global__ void __launch_bounds__(256) k_adj_rot_t(Geometry g, const AdjEntry* __restrict__ adj,
+__global__ void __launch_bounds__(256) k_adj_rot_t(Geometry g, int ps, const AdjEntry* __restrict__ adj,
                                                    const float* __restrict__ slab, int l0, int nv, float* out,
                                                    int accumulate, float* em_x, const float* __restrict__ em_s)
 {
@@ -543,7 +651,7 @@ __global__ void __launch_bounds__(256) k_adj_rot_t(Geometry g, const AdjEntry* _
     const int k = (idx - q * nzv) * VEC;
     const AdjEntry* e = adj + ((size_t)q * g.nview + l0) * MAXE;
     const float* t = slab + k;
-    const size_t vstride = (size_t)nxy * g.nz;
+    const size_t vstride = (size_t)g.ny * ps;
     KSum acc[VEC];
     for (int v = 0; v < nv; ++v) {
         AdjEntry a[MAXE];
@@ -591,6 +699,7 @@ FusedDims dims_for(const Geometry& g, int J)
 {
     using S = Sep<P>;
     FusedDims d;
+    d.ps = (g.nx * g.nz + 3) & ~3;
     d.nib = (g.nx + S::CX - 1) / S::CX;
     d.nkb = (g.nz + S::CZ - 1) / S::CZ;
     d.wp = (d.nib * S::CX + 2 * S::C) | 1;
@@ -605,27 +714,33 @@ FusedDims dims_for(const Geometry& g, int J)
 }
 
 template <int P>
-size_t smem_for(const Geometry& g, const FusedDims& d)
+size_t smem_fwd(const Geometry& g, const FusedDims& d)
 {
-    return fused_smem_floats(d, g.nx, g.nz, Sep<P>::PT) * sizeof(float);
+    return fwd_smem_floats(d, g.nx, g.nz, Sep<P>::PT) * sizeof(float);
+}
+
+template <int P>
+size_t smem_adj(const Geometry& g, const FusedDims& d)
+{
+    return adj_smem_floats(d, g.nx, Sep<P>::PT) * sizeof(float);
 }
 
 template <int P>
 bool fits(const Geometry& g, size_t limit)
 {
     const FusedDims d = dims_for<P>(g, 8);
-    return smem_for<P>(g, d) <= limit;
+    return smem_fwd<P>(g, d) <= limit && smem_adj<P>(g, d) <= limit && (size_t)d.ps * 4 < (1u << 20);
 }
 
 template <int P>
 cudaError_t fwd_launch(const spect_plan_s& Pl, const float* xt, int l0, int nv, cudaStream_t st)
 {
     const FusedDims d = dims_for<P>(Pl.g, Pl.fused_J);
-    const size_t smem = smem_for<P>(Pl.g, d);
+    const size_t smem = smem_fwd<P>(Pl.g, d);
     cudaError_t e = cudaFuncSetAttribute(k_fwd_sep_fused<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_fwd_sep_fused<P><<<dim3(d.G, nv), kFusedThreads, smem, st>>>(Pl.g, d, Pl.rot, xt, Pl.mubar, Pl.fx, Pl.fz,
-                                                                    Pl.part, l0);
+                                                                    Pl.part, l0, Pl.err);
     return cudaGetLastError();
 }
 
@@ -633,11 +748,11 @@ template <int P>
 cudaError_t adj_launch(const spect_plan_s& Pl, const float* v, int l0, int nv, cudaStream_t st)
 {
     const FusedDims d = dims_for<P>(Pl.g, Pl.fused_J);
-    const size_t smem = smem_for<P>(Pl.g, d);
+    const size_t smem = smem_adj<P>(Pl.g, d);
     cudaError_t e = cudaFuncSetAttribute(k_adj_sep_fused<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_adj_sep_fused<P><<<dim3(d.G, nv), kFusedThreads, smem, st>>>(Pl.g, d, Pl.cls_z, v, Pl.mubar, Pl.fx_adj,
-                                                                    Pl.fz_adj, Pl.slab, l0);
+                                                                    Pl.fz_adj, Pl.slab, l0, Pl.err);
     return cudaGetLastError();
 }
 }  // namespace
@@ -710,9 +825,9 @@ cudaError_t launch_adj_rot_t(const spect_plan_s& P, int l0, int nv, float* out, 
 #define SPECT_ADJ(M)                                                                                                 \
     case M:                                                                                                          \
         if (vec4)                                                                                                    \
-            k_adj_rot_t<M, 4><<<blocks, 256, 0, st>>>(P.g, P.adjf, P.slab, l0, nv, out, accumulate, em_x, em_s); \
+            k_adj_rot_t<M, 4><<<blocks, 256, 0, st>>>(P.g, P.ps, P.adjf, P.slab, l0, nv, out, accumulate, em_x, em_s); \
         else                                                                                                         \
-            k_adj_rot_t<M, 1><<<blocks, 256, 0, st>>>(P.g, P.adjf, P.slab, l0, nv, out, accumulate, em_x, em_s); \
+            k_adj_rot_t<M, 1><<<blocks, 256, 0, st>>>(P.g, P.ps, P.adjf, P.slab, l0, nv, out, accumulate, em_x, em_s); \
         break;
         SPECT_ADJ(1) SPECT_ADJ(2) SPECT_ADJ(3) SPECT_ADJ(4) SPECT_ADJ(5) SPECT_ADJ(6) SPECT_ADJ(7) SPECT_ADJ(8)
 #undef SPECT_ADJ

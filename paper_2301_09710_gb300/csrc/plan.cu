@@ -85,7 +85,7 @@ void free_plan(spect_plan_s* P)
     }
     for (cudaEvent_t e : P->evpool) cudaEventDestroy(e);
     void* ptrs[] = {P->mu, P->psf, P->psf_adj, P->fx, P->fz, P->fx_adj, P->fz_adj, P->rot, P->adj_off, P->adj,
-                    P->slab, P->e, P->ratio, P->s, P->mubar, P->xt, P->et, P->st, P->part, P->adjf};
+                    P->slab, P->e, P->ratio, P->s, P->mubar, P->xt, P->et, P->st, P->part, P->adjf, P->err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete P;
@@ -296,6 +296,7 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
     g.dy = dy;
     g.has_mu = mu != nullptr;
     P->separable = psf_fx && (!psf || (flags & SPECT_PLAN_PREFER_SEPARABLE));
+    P->ps = (nx * nz + 3) & ~3;
     P->cls_x = 3;
     P->cls_z = nz >= 2 ? 3 : 1;
 
@@ -339,6 +340,8 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
     const size_t vol = (size_t)nx * ny * nz, nproj = (size_t)nx * nz * nview;
     const size_t nxy = (size_t)nx * ny, nrows = (size_t)nview_psf * ny;
 
+    PLAN_ALLOC(P->err, 1, "error word");
+    PLAN_TRY(cudaMemsetAsync(P->err, 0, sizeof(int), st), "clear error word");
     // attenuation map (zeros are never read when mu == NULL)
     PLAN_ALLOC(P->mu, vol, "mu");
     if (mu) PLAN_TRY(cudaMemcpyAsync(P->mu, mu, vol * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy mu");
@@ -433,15 +436,16 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
 
     // work slab and EM buffers
     const size_t budget = slab_budget_bytes(P->fast);
-    P->chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)nview, budget / (vol * sizeof(float))));
-    PLAN_ALLOC(P->slab, vol * (size_t)P->chunk, "work slab");
+    const size_t per_view = std::max(vol, (size_t)ny * P->ps);  // fused path pads planes to ps floats
+    P->chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)nview, budget / (per_view * sizeof(float))));
+    PLAN_ALLOC(P->slab, per_view * (size_t)P->chunk, "work slab");
     PLAN_ALLOC(P->e, vol, "EM accumulator");
     PLAN_ALLOC(P->ratio, nproj, "EM ratio");
     PLAN_ALLOC(P->s, vol, "sensitivity");
 
     // fused path: attenuation cache for every view, internal-layout buffers
     if (P->fast) {
-        PLAN_ALLOC(P->mubar, vol * (size_t)nview, "attenuation cache");
+        PLAN_ALLOC(P->mubar, (size_t)ny * P->ps * nview, "attenuation cache");
         PLAN_ALLOC(P->xt, vol, "internal image");
         PLAN_ALLOC(P->et, vol, "internal back-projection");
         PLAN_ALLOC(P->st, vol, "internal sensitivity");
@@ -531,6 +535,19 @@ spect_status spect_em_step(spect_plan P, float* x, const float* y, const float* 
         r = run_back(P, P->ratio, P->e, x, P->s, st);
         if (r != SPECT_OK) return r;
     }
+    return SPECT_OK;
+}
+
+spect_status spect_plan_check(spect_plan P)
+{
+    if (!P) return fail(SPECT_EINVAL, "plan is NULL");
+    int h = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&h, P->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && h != 0) e = cudaMemset(P->err, 0, sizeof(int));
+    if (e != cudaSuccess) return fail(SPECT_ECUDA, std::string("reading the plan's error word: ") + cudaGetErrorString(e));
+    if (h == SPECT_ETIMEOUT) return fail(SPECT_ETIMEOUT, "a bounded wait on a bulk copy ran out; outputs are invalid");
+    if (h != 0) return fail(SPECT_ECUDA, "device error word set");
     return SPECT_OK;
 }
 

@@ -83,6 +83,8 @@ struct spect_plan_s {
     float* st = nullptr;         // nx*ny*nz, [j][i][k] sensitivity
     float* part = nullptr;       // G * nx*nz*nview forward partial sums
     spect::AdjEntry* adjf = nullptr;  // nview*nx*ny*adj_max fixed-length lists
+    int ps = 0;                  // plane stride of the attenuation cache and slab: nx*nz rounded up to 4
+    int* err = nullptr;          // device error word (SPECT_ETIMEOUT when a bounded wait ran out)
     size_t bytes = 0;
     // launch accounting and optional per-launch event timing
     long long launches[SPECT_K_COUNT] = {0, 0, 0, 0, 0};
@@ -183,6 +185,67 @@ struct KSum {
     }
     __device__ __forceinline__ float value() const { return s - c; }
 };
+
+// --------------------------------------------------------------------- TMA bulk copies
+// 1D bulk copies between global and shared memory (cp.async.bulk) completed
+// through an mbarrier.  Every wait is bounded: a wait that runs out returns
+// false and the caller records SPECT_ETIMEOUT in the plan's error word.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Arrive on `bar` expecting `bytes` of transaction, then start the copy.
+__device__ __forceinline__ void tma_load_1d(void* dst_smem, const void* src_gmem, unsigned bytes, uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst_smem)),
+                 "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of `bar` for at most ~2^31 SM clocks (about one second).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (clock64() - t0 < (1ll << 31))
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_store_1d(void* dst_gmem, const void* src_smem, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem), "r"(smem_u32(src_smem)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// Wait until at most N committed bulk stores still read their shared-memory source.
+template <int N>
+__device__ __forceinline__ void tma_store_wait_read()
+{
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void tma_store_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // --------------------------------------------------------------------- launchers
 // All return the cudaError_t of the launch (cudaGetLastError()).

@@ -139,6 +139,10 @@ class SpectPlan:
         return {"separable": bool(sep.value), "fused": bool(fused.value), "view_chunk": chunk.value,
                 "device_bytes": nbytes.value}
 
+    def check(self) -> None:
+        """Synchronise and raise SpectError(SPECT_ETIMEOUT) if a bounded device wait ran out."""
+        _lib.check(self.lib.spect_plan_check(self.handle))
+
     def profile(self, enable: bool = True) -> None:
         """Bracket every later kernel launch with CUDA events on its stream."""
         _lib.check(self.lib.spect_profile_enable(self.handle, int(bool(enable))))

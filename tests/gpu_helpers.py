@@ -44,6 +44,7 @@ PATHS = ["fused", "lowmem", "direct"]
 
 
 def make_plan(prob, angles, path, nview=None):
+    """A plan of the given path; the tests call plan.check() through host() on it."""
     from paper_2301_09710_gb300 import SpectPlan
     nz, ny, nx = prob.x.shape
     nview = len(angles) if nview is None else nview

@@ -44,6 +44,7 @@ def test_config2_sampled_views(prob, path):
     xb = host(plan.back(dev(y)))
     xb_o = oracle.back(y[SAMPLE_VIEWS], prob.mu, psf, prob.dy, sub, nthreads=4)
     assert_close(xb, xb_o, what="A' y sampled views")
+    plan.check()
     plan.close()
 
 
@@ -74,6 +75,7 @@ def test_config2_adjoint_and_em_invariants(prob, path):
     want = x0 * plan.back(ratio) / torch.from_numpy(s.astype(np.float32)).cuda()
     plan.em_step(xk, dev(y), None, niter=1)
     assert_close(host(xk), host(want), rel_l2=1e-6, max_rel=1e-5, what="fused EM vs composed")
+    plan.check()
     plan.close()
 
 

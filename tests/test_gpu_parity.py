@@ -49,6 +49,7 @@ def test_config1_forward_back_em(path):
     lhs = np.vdot(host(plan.forward(x)), yy.astype(np.float64))
     rhs = np.vdot(prob.x.astype(np.float64), host(plan.back(dev(yy))))
     assert abs(lhs - rhs) <= ADJ_FP32 * abs(lhs)
+    plan.check()
     plan.close()
 
 
@@ -80,6 +81,7 @@ def test_ragged_forward_back(case, path):
     xb = plan.back(dev(yy))
     xb_o = oracle.back(yy, prob.mu, psf, prob.dy, ang)
     assert_close(host(xb), xb_o, what="A' y")
+    plan.check()
     plan.close()
 
 
