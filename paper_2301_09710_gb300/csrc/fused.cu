@@ -114,6 +114,32 @@ cudaError_t launch_mubar_cache(const spect_plan_s& P, const float* mu_t, cudaStr
     return cudaGetLastError();
 }
 
+// Rotation tables of every (view, depth row), the per-plane input of the fused
+// forward: block (l, j) holds nx float4 weights then nx int bases (ts floats,
+// 16-byte aligned), fetched together with the attenuation plane by one TMA
+// transaction.
+__global__ void k_rot_tables(Geometry g, int ts, const ViewRot* __restrict__ rot, float* __restrict__ tab)
+{
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)g.nview * g.ny * g.nx) return;
+    const int i = (int)(idx % g.nx);
+    const size_t lj = idx / g.nx;
+    const int j = (int)(lj % g.ny), l = (int)(lj / g.ny);
+    float4 w;
+    int base;
+    rot_table_entry(i, j, rot[l], g, w, base);
+    float* blk = tab + lj * ts;
+    reinterpret_cast<float4*>(blk)[i] = w;
+    reinterpret_cast<int*>(blk + 4 * g.nx)[i] = base;
+}
+
+cudaError_t launch_rot_tables(const spect_plan_s& P, cudaStream_t st)
+{
+    const size_t n = (size_t)P.g.nview * P.g.ny * P.g.nx;
+    k_rot_tables<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.g, P.ts, P.rot, P.rtab);
+    return cudaGetLastError();
+}
+
 // Fixed-length adjacency lists for the transposed rotation: for destination
 // q and view l, up to `maxe` (source column offset j*ps + i*nz, weight) pairs,
 // zero-padded, laid out [q][l][e].  The candidate search and weights are those
@@ -202,12 +228,13 @@ struct FusedDims {
     int nib, nkb;
     int J, G;   // depth planes per block, depth groups
     int ps;     // plane stride of the attenuation cache / slab (nx*nz rounded up to 4)
+    int ts;     // rotation table block per (view, row): 5*nx rounded up to 4
 };
 
 __host__ __device__ inline size_t fwd_smem_floats(const FusedDims& d, int nx, int nz, int PT)
 {
-    // W | U | MB | taps 2x(FX,FZ) | table 2x(TW,TB) | ACC | mbarrier
-    return (size_t)d.warea + (size_t)nx * d.kpu + d.ps + 4 * (size_t)PT + 10 * (size_t)nx + (size_t)nx * nz + 4;
+    // W | U | MB | table (ts) | taps 2x(FX,FZ) | ACC | mbarrier
+    return (size_t)d.warea + (size_t)nx * d.kpu + d.ps + d.ts + 4 * (size_t)PT + (size_t)nx * nz + 4;
 }
 
 __host__ __device__ inline size_t adj_smem_floats(const FusedDims& d, int nx, int PT)
@@ -260,7 +287,7 @@ __device__ __forceinline__ void flag_timeout(int* err)
 
 template <int P>
 __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, FusedDims d,
-                                                                     const ViewRot* __restrict__ rot,
+                                                                     const float* __restrict__ rtab,
                                                                      const float* __restrict__ xt,
                                                                      const float* __restrict__ mubar,
                                                                      const float* __restrict__ fx,
@@ -273,24 +300,24 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     float* W = sm;
     float* U = W + d.warea;
-    float* MB = U + (size_t)nx * d.kpu;
-    float* TAP = MB + d.ps;                            // [2][FX PT | FZ PT]
-    float4* TW = reinterpret_cast<float4*>(TAP + 4 * PT);  // [2][nx]
-    int* TB = reinterpret_cast<int*>(TW + 2 * nx);         // [2][nx]
-    float* ACC = reinterpret_cast<float*>(TB + 2 * nx);    // nz x nx, [k][i]
+    float* MB = U + (size_t)nx * d.kpu;               // attenuation plane, then the rotation table
+    const float4* TW = reinterpret_cast<const float4*>(MB + d.ps);
+    const int* TB = reinterpret_cast<const int*>(MB + d.ps + 4 * nx);
+    float* TAP = MB + d.ps + d.ts;                     // [2][FX PT | FZ PT]
+    float* ACC = TAP + 4 * PT;                         // nz x nx, [k][i]
     uint64_t* bar = reinterpret_cast<uint64_t*>(ACC + (((size_t)nx * nz + 1) & ~(size_t)1));
     const int tid = threadIdx.x, lane = tid & 31;
     constexpr int T = kFusedThreads;
     const int grp = blockIdx.x, l = l0 + blockIdx.y;
     const int lp = g.nvp == 1 ? 0 : l;
     const int j_begin = grp * d.J, j_end = min(ny, j_begin + d.J);
-    const ViewRot r = rot[l];
     const int ox = (P - g.px) / 2, oz = (P - g.pz) / 2;  // zero-padding offsets of the taps
     const int pln = nx * nz;
     const int wcols = d.nib * CX + 2 * C;  // used W columns
     const float* mub = mubar + ((size_t)l * ny) * d.ps;
+    const float* tab = rtab + ((size_t)l * ny) * d.ts;
 
-    // taps (zero-padded to P, centred) and rotation table of plane j into buffer b
+    // taps (zero-padded to P, centred) of plane j into buffer b
     auto prepare = [&](int j, int b) {
         float* FX = TAP + b * 2 * PT;
         for (int a = tid; a < PT; a += T) {
@@ -298,7 +325,14 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
             FX[a] = (ax >= 0 && ax < g.px) ? __ldg(fx + ((size_t)lp * ny + j) * g.px + ax) : 0.f;
             FX[PT + a] = (az >= 0 && az < g.pz) ? __ldg(fz + ((size_t)lp * ny + j) * g.pz + az) : 0.f;
         }
-        for (int i = tid; i < nx; i += T) rot_table_entry(i, j, r, g, TW[b * nx + i], TB[b * nx + i]);
+    };
+    // attenuation plane and rotation table of plane j, one bulk transaction
+    auto fetch = [&](int j) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                     "r"((unsigned)(d.ps + d.ts) * 4u)
+                     : "memory");
+        tma_copy_1d(MB, mub + (size_t)j * d.ps, (unsigned)d.ps * 4u, bar);
+        tma_copy_1d(MB + d.ps, tab + (size_t)j * d.ts, (unsigned)d.ts * 4u, bar);
     };
 
     for (int e = tid; e < pln; e += T) ACC[e] = 0.f;
@@ -306,7 +340,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
     if (tid == 0) {
         mbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        tma_load_1d(MB, mub + (size_t)j_begin * d.ps, (unsigned)d.ps * 4u, bar);
+        fetch(j_begin);
     }
     __syncthreads();
 
@@ -315,21 +349,22 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
         const int b = (j - j_begin) & 1;
         const float* FX = TAP + b * 2 * PT;
         const float* FZ = FX + PT;
-        const float4* tw = TW + b * nx;
-        const int* tb = TB + b * nx;
+        const float4* tw = TW;
+        const int* tb = TB;
 
-        // rotate + attenuate the plane into W[k][C+i]; four points per thread
-        // per batch keep 16 independent gathers in flight
+        // rotate + attenuate the plane into W[k][C+i]; eight points per thread
+        // per batch keep 32 independent gathers in flight
         const bool ok = mbar_wait_bounded(bar, phase);
         phase ^= 1u;
         if (ok) {
+            constexpr int B = 8;
             const int sdi = T / nz, sdk = T - sdi * nz;  // (i,k) step of one stride T
             int ci = tid / nz, ck = tid - ci * nz;
-            for (int f0 = tid; f0 < pln; f0 += 4 * T) {
-                float xv[4][4];
-                int ii[4], kk[4];
+            for (int f0 = tid; f0 < pln; f0 += B * T) {
+                float xv[B][4];
+                int ii[B], kk[B];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < B; ++u) {
                     ii[u] = ci;
                     kk[u] = ck;
                     ck += sdk;
@@ -347,7 +382,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
                     }
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < B; ++u) {
                     if (f0 + u * T < pln) {
                         const float4 w = tw[ii[u]];
                         float v = w.x * xv[u][0];
@@ -372,10 +407,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
             }
             return;
         }
-        // MB is free again: bring in the next plane's attenuation
+        // MB and the table are free again: bring in the next plane's
         if (tid == 0 && j + 1 < j_end) {
             fence_proxy_async_smem();
-            tma_load_1d(MB, mub + (size_t)(j + 1) * d.ps, (unsigned)d.ps * 4u, bar);
+            fetch(j + 1);
         }
 
         // i-pass: U(i,k) = sum_a fx(a) w(clamp(i-a+cx), k); lanes over k.  The
@@ -400,8 +435,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
             }
             const unsigned m0 = __ballot_sync(0xffffffffu, valid && k == 0);
             const unsigned m1 = __ballot_sync(0xffffffffu, valid && k == nz - 1);
-            if (m0) {
-                const int src = __ffs(m0) - 1;
+            for (unsigned mm = m0; mm; mm &= mm - 1) {  // every lane of this warp holding k = 0
+                const int src = __ffs(mm) - 1;
                 const int i0s = __shfl_sync(0xffffffffu, i0, src);
 #pragma unroll
                 for (int c = 0; c < CX; ++c) {
@@ -410,8 +445,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
                         for (int h = lane; h < ZH; h += 32) U[(i0s + c) * d.kpu + h] = vv;
                 }
             }
-            if (m1) {
-                const int src = __ffs(m1) - 1;
+            for (unsigned mm = m1; mm; mm &= mm - 1) {  // every lane holding k = nz-1
+                const int src = __ffs(mm) - 1;
                 const int i0s = __shfl_sync(0xffffffffu, i0, src);
                 const int nr = d.kpu - ZH - nz;
 #pragma unroll
@@ -700,6 +735,7 @@ FusedDims dims_for(const Geometry& g, int J)
     using S = Sep<P>;
     FusedDims d;
     d.ps = (g.nx * g.nz + 3) & ~3;
+    d.ts = (5 * g.nx + 3) & ~3;
     d.nib = (g.nx + S::CX - 1) / S::CX;
     d.nkb = (g.nz + S::CZ - 1) / S::CZ;
     d.wp = (d.nib * S::CX + 2 * S::C) | 1;
@@ -739,7 +775,7 @@ cudaError_t fwd_launch(const spect_plan_s& Pl, const float* xt, int l0, int nv, 
     const size_t smem = smem_fwd<P>(Pl.g, d);
     cudaError_t e = cudaFuncSetAttribute(k_fwd_sep_fused<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_fwd_sep_fused<P><<<dim3(d.G, nv), kFusedThreads, smem, st>>>(Pl.g, d, Pl.rot, xt, Pl.mubar, Pl.fx, Pl.fz,
+    k_fwd_sep_fused<P><<<dim3(d.G, nv), kFusedThreads, smem, st>>>(Pl.g, d, Pl.rtab, xt, Pl.mubar, Pl.fx, Pl.fz,
                                                                     Pl.part, l0, Pl.err);
     return cudaGetLastError();
 }

@@ -85,7 +85,7 @@ void free_plan(spect_plan_s* P)
     }
     for (cudaEvent_t e : P->evpool) cudaEventDestroy(e);
     void* ptrs[] = {P->mu, P->psf, P->psf_adj, P->fx, P->fz, P->fx_adj, P->fz_adj, P->rot, P->adj_off, P->adj,
-                    P->slab, P->e, P->ratio, P->s, P->mubar, P->xt, P->et, P->st, P->part, P->adjf, P->err};
+                    P->slab, P->e, P->ratio, P->s, P->mubar, P->xt, P->et, P->st, P->part, P->adjf, P->err, P->rtab};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete P;
@@ -297,6 +297,7 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
     g.has_mu = mu != nullptr;
     P->separable = psf_fx && (!psf || (flags & SPECT_PLAN_PREFER_SEPARABLE));
     P->ps = (nx * nz + 3) & ~3;
+    P->ts = (5 * nx + 3) & ~3;
     P->cls_x = 3;
     P->cls_z = nz >= 2 ? 3 : 1;
 
@@ -453,6 +454,8 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
         // mu in the [j][i][k] layout (temporary, the slab serves as scratch)
         PLAN_TRY(spect::launch_transpose(P->mu, P->slab, nz, (int)nxy, st), "mu transpose launch");
         PLAN_TRY(spect::launch_mubar_cache(*P, P->slab, st), "attenuation cache launch");
+        PLAN_ALLOC(P->rtab, (size_t)nview * ny * P->ts, "rotation tables");
+        PLAN_TRY(spect::launch_rot_tables(*P, st), "rotation table launch");
     }
     PLAN_TRY(cudaStreamSynchronize(st), "plan set-up");
     *out = P;

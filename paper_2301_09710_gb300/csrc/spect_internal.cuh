@@ -84,6 +84,8 @@ struct spect_plan_s {
     float* part = nullptr;       // G * nx*nz*nview forward partial sums
     spect::AdjEntry* adjf = nullptr;  // nview*nx*ny*adj_max fixed-length lists
     int ps = 0;                  // plane stride of the attenuation cache and slab: nx*nz rounded up to 4
+    int ts = 0;                  // rotation table block per (view, row): 5*nx rounded up to 4
+    float* rtab = nullptr;       // nview*ny*ts rotation tables of the fused forward
     int* err = nullptr;          // device error word (SPECT_ETIMEOUT when a bounded wait ran out)
     size_t bytes = 0;
     // launch accounting and optional per-launch event timing
@@ -199,14 +201,20 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
 
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Arrive on `bar` expecting `bytes` of transaction, then start the copy.
-__device__ __forceinline__ void tma_load_1d(void* dst_smem, const void* src_gmem, unsigned bytes, uint64_t* bar)
+// Start a bulk copy global -> shared whose bytes complete on `bar`.
+__device__ __forceinline__ void tma_copy_1d(void* dst_smem, const void* src_gmem, unsigned bytes, uint64_t* bar)
 {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      smem_u32(dst_smem)),
                  "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
+}
+
+// Arrive on `bar` expecting `bytes` of transaction, then start the copy.
+__device__ __forceinline__ void tma_load_1d(void* dst_smem, const void* src_gmem, unsigned bytes, uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    tma_copy_1d(dst_smem, src_gmem, bytes, bar);
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
@@ -264,6 +272,7 @@ int fused_groups(const spect_plan_s& P);
 cudaError_t launch_transpose(const float* in, float* out, int R, int C, cudaStream_t st);
 cudaError_t launch_mubar_cache(const spect_plan_s& P, const float* mu_t, cudaStream_t st);
 cudaError_t launch_build_adjacency_fixed(const spect_plan_s& P, cudaStream_t st);
+cudaError_t launch_rot_tables(const spect_plan_s& P, cudaStream_t st);
 cudaError_t launch_fused_forward(const spect_plan_s& P, const float* xt, int l0, int nv, cudaStream_t st);
 cudaError_t launch_fused_adjoint(const spect_plan_s& P, const float* v, int l0, int nv, cudaStream_t st);
 cudaError_t launch_fwd_reduce(const spect_plan_s& P, float* v, const float* em_y, const float* em_rbar,
