@@ -220,6 +220,32 @@ spect_status spect_plan_check(spect_plan plan);
  * Waits for the plan's outstanding work on the device before freeing. */
 spect_status spect_plan_destroy(spect_plan plan);
 
+/*
+ * spect_forward_static -- v = A x without any device allocation.
+ *
+ * For callers that cannot allocate device memory (code running while a CUDA
+ * graph is captured, hosts whose device memory is reserved up front, plug-in
+ * environments that own the allocator).  No plan is needed: the call takes
+ * the same inputs as spect_plan_create (separable PSF factors only) plus x and
+ * v, and uses a work slab and rotation constants held in fixed-size static
+ * device arrays of the library (the paper has no counterpart).  Nothing is
+ * allocated, by this call or by anything it calls.
+ *   nx..angles  as spect_plan_create (psf_fx, psf_fz required; mu may be NULL;
+ *               angles is a HOST array or NULL).
+ *   x           device, nx*ny*nz image; v device, nx*nz*nview, overwritten.
+ * Limits: nx*ny*nz <= 8388608 voxels and nview <= 4096, else SPECT_EINVAL.
+ * The static arrays (32 MiB + 64 KiB) are held by every device that loads the
+ * library until the process exits.  The first call on a device looks up
+ * their device addresses (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the arrays: calls that overlap on the
+ * GPU (other streams or host threads) race and must be serialised.
+ * Errors: SPECT_EINVAL (arguments, sizes beyond the limits), SPECT_EUNSUPPORTED,
+ * SPECT_ECUDA.
+ */
+spect_status spect_forward_static(int nx, int ny, int nz, int nview, const float* x, const float* mu, float dy,
+                                  const float* psf_fx, const float* psf_fz, int px, int pz, int nview_psf,
+                                  const double* angles, float* v, spect_stream stream);
+
 /* Thread-local message for the last non-OK status returned on this thread
  * ("" if none).  The pointer stays valid until the next call on the thread. */
 const char* spect_last_error(void);

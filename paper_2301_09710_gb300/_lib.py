@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH):
         lib.spect_profile_read.restype = st
         lib.spect_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
         lib.spect_fp32_peak.restype = st
+        lib.spect_forward_static.argtypes = [i, i, i, i, vp, vp, ctypes.c_float, vp, vp, i, i, i, vp, vp, vp]
+        lib.spect_forward_static.restype = st
         lib.spect_plan_check.argtypes = [vp]
         lib.spect_plan_check.restype = st
         lib.spect_plan_destroy.argtypes = [vp]

@@ -15,6 +15,10 @@
 using spect::Geometry;
 using spect::ViewRot;
 
+namespace spect {
+void make_view_rot(int nx, int nview, const double* angles, ViewRot* out);
+}
+
 namespace {
 
 thread_local std::string g_err;
@@ -58,6 +62,26 @@ void split(double t, int h, float* hi, float* lo)
     *hi = (float)th;
     *lo = (float)(t - th);
 }
+
+}  // namespace
+
+// Per-view rotation constants (see rot_sample()): cos/sin split into a part
+// on a 2^-h grid, h chosen from nx so the products with (i - c) are exact.
+void spect::make_view_rot(int nx, int nview, const double* angles, ViewRot* out)
+{
+    int lg = 0;
+    while ((1 << lg) < nx) ++lg;
+    const int h = 22 - lg;
+    for (int l = 0; l < nview; ++l) {
+        const double th = angles ? angles[l] : 2.0 * M_PI * (double)l / (double)nview;
+        double c, s;
+        exact_cos_sin(th, &c, &s);
+        split(c, h, &out[l].ct_hi, &out[l].ct_lo);
+        split(s, h, &out[l].st_hi, &out[l].st_lo);
+    }
+}
+
+namespace {
 
 template <class T>
 spect_status dalloc(spect_plan_s* P, T** p, size_t count, const char* what)
@@ -253,6 +277,9 @@ spect_status check_call(spect_plan P, const void* a, const void* b, const char* 
 
 }  // namespace
 
+// Record a status and message for spect_last_error() (other translation units).
+spect_status spect::set_error(spect_status st, const char* msg) { return fail(st, msg); }
+
 extern "C" {
 
 const char* spect_last_error(void) { return g_err.c_str(); }
@@ -375,17 +402,8 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
 
     // per-view rotation constants
     {
-        int lg = 0;
-        while ((1 << lg) < nx) ++lg;
-        const int h = 22 - lg;
         std::vector<ViewRot> vr(nview);
-        for (int l = 0; l < nview; ++l) {
-            const double th = angles ? angles[l] : 2.0 * M_PI * (double)l / (double)nview;
-            double c, s;
-            exact_cos_sin(th, &c, &s);
-            split(c, h, &vr[l].ct_hi, &vr[l].ct_lo);
-            split(s, h, &vr[l].st_hi, &vr[l].st_lo);
-        }
+        spect::make_view_rot(nx, nview, angles, vr.data());
         PLAN_ALLOC(P->rot, (size_t)nview, "rotation constants");
         PLAN_TRY(cudaMemcpyAsync(P->rot, vr.data(), nview * sizeof(ViewRot), cudaMemcpyHostToDevice, st),
                  "upload rotation constants");

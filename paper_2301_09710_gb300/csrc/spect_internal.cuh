@@ -256,6 +256,11 @@ __device__ __forceinline__ void tma_store_wait_read()
 __device__ __forceinline__ void tma_store_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // --------------------------------------------------------------------- launchers
+// Host: per-view rotation constants for nview angles (NULL: 2 pi l / nview).
+void make_view_rot(int nx, int nview, const double* angles, ViewRot* out);
+// Host: record `st` and `msg` for spect_last_error() on this thread; returns st.
+spect_status set_error(spect_status st, const char* msg);
+
 // All return the cudaError_t of the launch (cudaGetLastError()).
 cudaError_t launch_build_adjacency(const spect_plan_s& P, int pass, int* counts, int* maxcount, cudaStream_t st);
 cudaError_t launch_rotate_atten(const spect_plan_s& P, const float* x, int l0, int nv, cudaStream_t st);

@@ -45,6 +45,29 @@ def fp32_peak(stream=None) -> dict:
     return {"ffma_tflops": a.value, "ffma2_tflops": b.value}
 
 
+def forward_static(x, nview: int, fx, fz, mu=None, dy: float = 1.0, angles=None, out=None, stream=None):
+    """v = A x through spect_forward_static: no plan, no device allocation in
+    the library (for callers that cannot allocate; see include/spect.h).
+
+    x, mu: (nz, ny, nx); fx: (nview_psf, ny, px); fz: (nview_psf, ny, pz), all
+    contiguous float32 CUDA tensors; out: (nview, nz, nx) or None (allocated
+    here by torch, outside the library call).
+    """
+    lib = _lib.load()
+    nz, ny, nx = x.shape
+    nvp, _, px = fx.shape
+    pz = fz.shape[-1]
+    if out is None:
+        out = torch.empty((nview, nz, nx), device=x.device, dtype=torch.float32)
+    ang = None
+    if angles is not None:
+        a = np.ascontiguousarray(np.asarray(angles, dtype=np.float64))
+        ang = a.ctypes.data_as(ctypes.c_void_p)
+    _lib.check(lib.spect_forward_static(nx, ny, nz, int(nview), _ptr(x), _ptr(mu), ctypes.c_float(dy), _ptr(fx),
+                                        _ptr(fz), px, pz, nvp, ang, _ptr(out), _stream_handle(stream)))
+    return out
+
+
 class SpectPlan:
     """The operator A of one geometry (Algorithm 1 inputs) on one GPU."""
 
