@@ -204,7 +204,8 @@ cudaError_t launch_build_adjacency_fixed(const spect_plan_s& P, cudaStream_t st)
 //   MB  the attenuation plane mubar(:, j, :) of the current depth, brought in
 //       by one TMA bulk copy issued a plane ahead.
 //   taps and rotation table of the current and the next plane (double buffer),
-//   ACC nz x nx depth-sum accumulators of the group, [k][i].
+//   ACC nx x apc depth-sum accumulators of the group, [i][k] (apc/4 odd, so
+//       the k-pass float4 read-modify-writes are bank-conflict free).
 // Per plane there are three block barriers: after the rotation, after the
 // i-pass, after the k-pass (which also prepares the next plane's table/taps).
 // ============================================================================
@@ -229,12 +230,13 @@ struct FusedDims {
     int J, G;   // depth planes per block, depth groups
     int ps;     // plane stride of the attenuation cache / slab (nx*nz rounded up to 4)
     int ts;     // rotation table block per (view, row): 5*nx rounded up to 4
+    int apc;    // accumulator row pitch (>= nkb*CZ, multiple of 4, pitch/4 odd)
 };
 
 __host__ __device__ inline size_t fwd_smem_floats(const FusedDims& d, int nx, int nz, int PT)
 {
     // W | U | MB | table (ts) | taps 2x(FX,FZ) | ACC | mbarrier
-    return (size_t)d.warea + (size_t)nx * d.kpu + d.ps + d.ts + 4 * (size_t)PT + (size_t)nx * nz + 4;
+    return (size_t)d.warea + (size_t)nx * d.kpu + d.ps + d.ts + 4 * (size_t)PT + (size_t)nx * d.apc + 4;
 }
 
 __host__ __device__ inline size_t adj_smem_floats(const FusedDims& d, int nx, int PT)
@@ -304,10 +306,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
     const float4* TW = reinterpret_cast<const float4*>(MB + d.ps);
     const int* TB = reinterpret_cast<const int*>(MB + d.ps + 4 * nx);
     float* TAP = MB + d.ps + d.ts;                     // [2][FX PT | FZ PT]
-    float* ACC = TAP + 4 * PT;                         // nz x nx, [k][i]
-    uint64_t* bar = reinterpret_cast<uint64_t*>(ACC + (((size_t)nx * nz + 1) & ~(size_t)1));
-    const int tid = threadIdx.x, lane = tid & 31;
-    constexpr int T = kFusedThreads;
+    float* ACC = TAP + 4 * PT;                         // nx x apc, [i][k]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(ACC + (size_t)nx * d.apc);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int T = kFusedThreads, NW = kFusedThreads / 32;
     const int grp = blockIdx.x, l = l0 + blockIdx.y;
     const int lp = g.nvp == 1 ? 0 : l;
     const int j_begin = grp * d.J, j_end = min(ny, j_begin + d.J);
@@ -335,7 +337,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
         tma_copy_1d(MB + d.ps, tab + (size_t)j * d.ts, (unsigned)d.ts * 4u, bar);
     };
 
-    for (int e = tid; e < pln; e += T) ACC[e] = 0.f;
+    for (int e = tid; e < nx * d.apc; e += T) ACC[e] = 0.f;
     prepare(j_begin, 0);
     if (tid == 0) {
         mbar_init(bar, 1);
@@ -349,53 +351,62 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
         const int b = (j - j_begin) & 1;
         const float* FX = TAP + b * 2 * PT;
         const float* FZ = FX + PT;
-        const float4* tw = TW;
-        const int* tb = TB;
 
-        // rotate + attenuate the plane into W[k][C+i]; eight points per thread
-        // per batch keep 32 independent gathers in flight
+        // rotate + attenuate the plane into W[k][C+i]: a warp per pair of
+        // rows i, lanes over k (up to 128 k per pass), so the table entry and
+        // the four corner pointers are warp-uniform and 32 gathers per warp
+        // are in flight; replicate halo columns come from the first/last row
         const bool ok = mbar_wait_bounded(bar, phase);
         phase ^= 1u;
         if (ok) {
-            constexpr int B = 8;
-            const int sdi = T / nz, sdk = T - sdi * nz;  // (i,k) step of one stride T
-            int ci = tid / nz, ck = tid - ci * nz;
-            for (int f0 = tid; f0 < pln; f0 += B * T) {
-                float xv[B][4];
-                int ii[B], kk[B];
+            for (int i = 2 * warp; i < nx; i += 2 * NW) {
+                const bool two = i + 1 < nx;
+                const float4 wa = TW[i];
+                const float4 wb = two ? TW[i + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float* pa = xt + (size_t)TB[i] * nz;
+                const float* pb = xt + (size_t)(two ? TB[i + 1] : TB[i]) * nz;
+                for (int k0 = 0; k0 < nz; k0 += 128) {
+                    float xa[4][4], xb[4][4];
 #pragma unroll
-                for (int u = 0; u < B; ++u) {
-                    ii[u] = ci;
-                    kk[u] = ck;
-                    ck += sdk;
-                    ci += sdi;
-                    if (ck >= nz) {
-                        ck -= nz;
-                        ++ci;
+                    for (int q = 0; q < 4; ++q) {
+                        const int k = k0 + 32 * q + lane;
+                        if (k < nz) {
+                            xa[q][0] = __ldg(pa + k);
+                            xa[q][1] = __ldg(pa + nz + k);
+                            xa[q][2] = __ldg(pa + pln + k);
+                            xa[q][3] = __ldg(pa + pln + nz + k);
+                            xb[q][0] = __ldg(pb + k);
+                            xb[q][1] = __ldg(pb + nz + k);
+                            xb[q][2] = __ldg(pb + pln + k);
+                            xb[q][3] = __ldg(pb + pln + nz + k);
+                        }
                     }
-                    if (f0 + u * T < pln) {
-                        const float* xb = xt + (tb[ii[u]] * nz + kk[u]);
-                        xv[u][0] = __ldg(xb);
-                        xv[u][1] = __ldg(xb + nz);
-                        xv[u][2] = __ldg(xb + pln);
-                        xv[u][3] = __ldg(xb + pln + nz);
-                    }
-                }
 #pragma unroll
-                for (int u = 0; u < B; ++u) {
-                    if (f0 + u * T < pln) {
-                        const float4 w = tw[ii[u]];
-                        float v = w.x * xv[u][0];
-                        v = fmaf(w.y, xv[u][1], v);
-                        v = fmaf(w.z, xv[u][2], v);
-                        v = fmaf(w.w, xv[u][3], v);
-                        v *= MB[f0 + u * T];
-                        float* wr = W + kk[u] * d.wp;
-                        wr[C + ii[u]] = v;
-                        if (ii[u] == 0)  // replicate padding along i: left halo columns
-                            for (int h = 0; h < C; ++h) wr[h] = v;
-                        if (ii[u] == nx - 1)  // right halo columns
-                            for (int h = C + nx; h < wcols; ++h) wr[h] = v;
+                    for (int q = 0; q < 4; ++q) {
+                        const int k = k0 + 32 * q + lane;
+                        if (k < nz) {
+                            float* wr = W + k * d.wp + C;
+                            float va = wa.x * xa[q][0];
+                            va = fmaf(wa.y, xa[q][1], va);
+                            va = fmaf(wa.z, xa[q][2], va);
+                            va = fmaf(wa.w, xa[q][3], va);
+                            va *= MB[i * nz + k];
+                            wr[i] = va;
+                            if (two) {
+                                float vb = wb.x * xb[q][0];
+                                vb = fmaf(wb.y, xb[q][1], vb);
+                                vb = fmaf(wb.z, xb[q][2], vb);
+                                vb = fmaf(wb.w, xb[q][3], vb);
+                                vb *= MB[(i + 1) * nz + k];
+                                wr[i + 1] = vb;
+                                if (i + 1 == nx - 1)
+                                    for (int h = nx; h < wcols - C; ++h) wr[h] = vb;
+                            }
+                            if (i == 0)
+                                for (int h = -C; h < 0; ++h) wr[h] = va;
+                            if (i == nx - 1)
+                                for (int h = nx; h < wcols - C; ++h) wr[h] = va;
+                        }
                     }
                 }
             }
@@ -429,9 +440,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
 #pragma unroll
                 for (int m = 0; m < CX + P - 1; ++m) win[m] = wr[m];
                 fir<P, CX, -1, P - 1>(FX, win, o);
+                float* ur = U + i0 * d.kpu + ZH + k;
+                if (i0 + CX <= nx) {
 #pragma unroll
-                for (int c = 0; c < CX; ++c)
-                    if (i0 + c < nx) U[(i0 + c) * d.kpu + ZH + k] = o[c];
+                    for (int c = 0; c < CX; ++c) ur[c * d.kpu] = o[c];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < CX; ++c)
+                        if (i0 + c < nx) ur[c * d.kpu] = o[c];
+                }
             }
             const unsigned m0 = __ballot_sync(0xffffffffu, valid && k == 0);
             const unsigned m1 = __ballot_sync(0xffffffffu, valid && k == nz - 1);
@@ -468,16 +485,26 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
             load_window_f4<P>(U + i * d.kpu + kb * CZ, win);
             float o[CZ];
             fir<P, CZ, -1, C + ZH>(FZ, win, o);
+            float4* acc4 = reinterpret_cast<float4*>(ACC + i * d.apc + kb * CZ);
 #pragma unroll
-            for (int c = 0; c < CZ; ++c)
-                if (kb * CZ + c < nz) ACC[(kb * CZ + c) * nx + i] += o[c];
+            for (int c4 = 0; c4 < CZ / 4; ++c4) {
+                float4 a = acc4[c4];
+                a.x += o[4 * c4];
+                a.y += o[4 * c4 + 1];
+                a.z += o[4 * c4 + 2];
+                a.w += o[4 * c4 + 3];
+                acc4[c4] = a;
+            }
         }
         __syncthreads();
     }
 
     // partial depth sums of this group: part[grp][l][k][i]
     float* pout = part + ((size_t)grp * g.nview + l) * pln;
-    for (int e = tid; e < pln; e += T) pout[e] = ACC[e];
+    for (int e = tid; e < pln; e += T) {
+        const int k = e / nx, i = e - k * nx;
+        pout[e] = ACC[i * d.apc + k];
+    }
 }
 
 // v(i,k,l) = sum over depth groups of the partials (fixed order), optionally
@@ -744,6 +771,9 @@ FusedDims dims_for(const Geometry& g, int J)
     kpu = (kpu + 3) & ~3;
     if (((kpu / 4) & 1) == 0) kpu += 4;
     d.kpu = kpu;
+    int apc = d.nkb * S::CZ;
+    if (((apc / 4) & 1) == 0) apc += 4;
+    d.apc = apc;
     d.J = J;
     d.G = (g.ny + J - 1) / J;
     return d;
