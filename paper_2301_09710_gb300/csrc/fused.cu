@@ -193,21 +193,21 @@ cudaError_t launch_build_adjacency_fixed(const spect_plan_s& P, cudaStream_t st)
 // ============================================================================
 // Fused forward, separable PSF, padded tap count P (odd).
 //
-// Shared-memory layout of one block (view l, depth group):
-//   W   nz rows x wp columns: the rotated, attenuated plane, W[k][C + i], with
-//       replicate halo columns; wp is odd so column-wise stores and the i-pass
-//       windows (lanes over k) are bank-conflict free, and every window load
-//       of the i-pass is an immediate offset from one base.
+// The forward runs as two kernels: k_rot_fwd rotates and attenuates every
+// (view, depth) plane into the work slab, already in the blur kernel's
+// shared-memory image; k_fwd_sep_fused (one block per view and depth group)
+// streams those images in by TMA and blurs them.  Its shared memory:
+//   W   two plane buffers, nz rows x wp columns: W[k][C + i] with replicate
+//       halo columns; wp is odd so the i-pass windows (lanes over k) are
+//       bank-conflict free and every window load is an immediate offset.
 //   U   nx rows x kpu: i-pass output, U[i][ZH + k], with replicate halo
 //       columns; kpu/4 is odd so the k-pass float4 windows (lanes over i) are
 //       bank-conflict free.
-//   MB  the attenuation plane mubar(:, j, :) of the current depth, brought in
-//       by one TMA bulk copy issued a plane ahead.
-//   taps and rotation table of the current and the next plane (double buffer),
+//   taps of every plane of the group, staged once.
 //   ACC nx x apc depth-sum accumulators of the group, [i][k] (apc/4 odd, so
 //       the k-pass float4 read-modify-writes are bank-conflict free).
-// Per plane there are three block barriers: after the rotation, after the
-// i-pass, after the k-pass (which also prepares the next plane's table/taps).
+// Per plane there are two block barriers: after the i-pass (which also agrees
+// on the bounded TMA wait) and after the k-pass.
 // ============================================================================
 template <int P>
 struct Sep {
@@ -235,14 +235,14 @@ struct FusedDims {
 
 __host__ __device__ inline size_t fwd_smem_floats(const FusedDims& d, int nx, int nz, int PT)
 {
-    // W | U | MB | table (ts) | taps 2x(FX,FZ) | ACC | mbarrier
-    return (size_t)d.warea + (size_t)nx * d.kpu + d.ps + d.ts + 4 * (size_t)PT + (size_t)nx * d.apc + 4;
+    // W x2 | U | taps J x (FX,FZ) | ACC | 2 mbarriers
+    return 2 * (size_t)d.warea + (size_t)nx * d.kpu + 2 * (size_t)PT * d.J + (size_t)nx * d.apc + 8;
 }
 
 __host__ __device__ inline size_t adj_smem_floats(const FusedDims& d, int nx, int PT)
 {
-    // Zb | V | MB x2 | taps 2x(FX[3],FZ[3]) | 2 mbarriers
-    return (size_t)d.warea + (size_t)nx * d.kpu + 2 * (size_t)d.ps + 12 * (size_t)PT + 8;
+    // Zb | V | MB x2 | taps J x (FX[3],FZ[3]) | 2 mbarriers
+    return (size_t)d.warea + (size_t)nx * d.kpu + 2 * (size_t)d.ps + 6 * (size_t)PT * d.J + 8;
 }
 
 template <int P>
@@ -287,11 +287,107 @@ __device__ __forceinline__ void flag_timeout(int* err)
     if (err) atomicExch(err, (int)SPECT_ETIMEOUT);
 }
 
+// ----------------------------------------------------------------------------
+// Forward rotation: one block per (depth plane j, view).  Warps take pairs of
+// rows i with lanes over k, so the table entry and the four corner pointers
+// are warp-uniform and every gather is a coalesced run along k (96 k per
+// pass, 30 independent loads per lane in flight).  The plane is
+// assembled in shared memory exactly as the blur kernel wants it -- W[k][C+i]
+// with replicate halo columns and odd pitch wp -- and leaves with one TMA bulk
+// store, so the blur kernel can bring it back with one bulk load.
+// ----------------------------------------------------------------------------
+constexpr int kRotThreads = 512;
+
+template <int P>
+__global__ void __launch_bounds__(kRotThreads, 2) k_rot_fwd(Geometry g, FusedDims d, const float* __restrict__ rtab,
+                                                         const float* __restrict__ xt,
+                                                         const float* __restrict__ mubar, float* __restrict__ wsl,
+                                                         int l0)
+{
+    constexpr int C = Sep<P>::C;
+    extern __shared__ __align__(16) float sm[];
+    float* S = sm;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = kRotThreads / 32;
+    const int j = blockIdx.x, v = blockIdx.y, l = l0 + v;
+    const int pln = nx * nz;
+    const int wcols = d.nib * Sep<P>::CX + 2 * C;
+    const float* tab = rtab + ((size_t)l * ny + j) * d.ts;
+    const float4* TW = reinterpret_cast<const float4*>(tab);
+    const int* TB = reinterpret_cast<const int*>(tab + 4 * nx);
+    const float* mb = mubar + ((size_t)l * ny + j) * d.ps;
+
+    for (int i = 2 * warp; i < nx; i += 2 * NW) {
+        const bool two = i + 1 < nx;
+        const float4 wa = __ldg(TW + i);
+        const float4 wb = two ? __ldg(TW + i + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float* pa = xt + (size_t)__ldg(TB + i) * nz;
+        const float* pb = xt + (size_t)__ldg(TB + (two ? i + 1 : i)) * nz;
+        for (int k0 = 0; k0 < nz; k0 += 96) {
+            float xa[3][4], xb[3][4], ma[3], mc[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int k = k0 + 32 * q + lane;
+                if (k < nz) {
+                    xa[q][0] = __ldg(pa + k);
+                    xa[q][1] = __ldg(pa + nz + k);
+                    xa[q][2] = __ldg(pa + pln + k);
+                    xa[q][3] = __ldg(pa + pln + nz + k);
+                    xb[q][0] = __ldg(pb + k);
+                    xb[q][1] = __ldg(pb + nz + k);
+                    xb[q][2] = __ldg(pb + pln + k);
+                    xb[q][3] = __ldg(pb + pln + nz + k);
+                    ma[q] = __ldg(mb + i * nz + k);
+                    mc[q] = two ? __ldg(mb + (i + 1) * nz + k) : 0.f;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int k = k0 + 32 * q + lane;
+                if (k < nz) {
+                    float* wr = S + k * d.wp + C;
+                    float va = wa.x * xa[q][0];
+                    va = fmaf(wa.y, xa[q][1], va);
+                    va = fmaf(wa.z, xa[q][2], va);
+                    va = fmaf(wa.w, xa[q][3], va);
+                    va *= ma[q];
+                    wr[i] = va;
+                    if (two) {
+                        float vb = wb.x * xb[q][0];
+                        vb = fmaf(wb.y, xb[q][1], vb);
+                        vb = fmaf(wb.z, xb[q][2], vb);
+                        vb = fmaf(wb.w, xb[q][3], vb);
+                        vb *= mc[q];
+                        wr[i + 1] = vb;
+                        if (i + 1 == nx - 1)
+                            for (int h = nx; h < wcols - C; ++h) wr[h] = vb;
+                    }
+                    if (i == 0)  // replicate padding along i: left halo columns
+                        for (int h = -C; h < 0; ++h) wr[h] = va;
+                    if (i == nx - 1)  // right halo columns
+                        for (int h = nx; h < wcols - C; ++h) wr[h] = va;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        tma_store_1d(wsl + ((size_t)v * ny + j) * d.warea, S, (unsigned)d.warea * 4u);
+        tma_store_wait_all();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Forward blur + depth sum: one block per (view, group of J depth planes).
+// Rotated planes arrive by TMA into a double buffer (plane j+2 is requested as
+// soon as plane j's i-pass has read its buffer); per plane the i-pass writes U
+// (k halos by warp shuffles), the k-pass accumulates into ACC.
+// ----------------------------------------------------------------------------
 template <int P>
 __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, FusedDims d,
-                                                                     const float* __restrict__ rtab,
-                                                                     const float* __restrict__ xt,
-                                                                     const float* __restrict__ mubar,
+                                                                     const float* __restrict__ wsl,
                                                                      const float* __restrict__ fx,
                                                                      const float* __restrict__ fz,
                                                                      float* __restrict__ part, int l0, int* err)
@@ -300,137 +396,54 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
     constexpr int C = S::C, CX = S::CX, CZ = S::CZ, ZH = S::ZH, WZ = S::WZ, PT = S::PT;
     extern __shared__ __align__(16) float sm[];
     const int nx = g.nx, ny = g.ny, nz = g.nz;
-    float* W = sm;
-    float* U = W + d.warea;
-    float* MB = U + (size_t)nx * d.kpu;               // attenuation plane, then the rotation table
-    const float4* TW = reinterpret_cast<const float4*>(MB + d.ps);
-    const int* TB = reinterpret_cast<const int*>(MB + d.ps + 4 * nx);
-    float* TAP = MB + d.ps + d.ts;                     // [2][FX PT | FZ PT]
-    float* ACC = TAP + 4 * PT;                         // nx x apc, [i][k]
+    float* WB = sm;                                    // [2][warea]
+    float* U = WB + 2 * (size_t)d.warea;
+    float* TAP = U + (size_t)nx * d.kpu;               // [J][FX PT | FZ PT], every plane of the group
+    float* ACC = TAP + 2 * PT * (size_t)d.J;           // nx x apc, [i][k]
     uint64_t* bar = reinterpret_cast<uint64_t*>(ACC + (size_t)nx * d.apc);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int T = kFusedThreads, NW = kFusedThreads / 32;
-    const int grp = blockIdx.x, l = l0 + blockIdx.y;
+    const int tid = threadIdx.x, lane = tid & 31;
+    constexpr int T = kFusedThreads;
+    const int grp = blockIdx.x, v = blockIdx.y, l = l0 + v;
     const int lp = g.nvp == 1 ? 0 : l;
     const int j_begin = grp * d.J, j_end = min(ny, j_begin + d.J);
     const int ox = (P - g.px) / 2, oz = (P - g.pz) / 2;  // zero-padding offsets of the taps
     const int pln = nx * nz;
-    const int wcols = d.nib * CX + 2 * C;  // used W columns
-    const float* mub = mubar + ((size_t)l * ny) * d.ps;
-    const float* tab = rtab + ((size_t)l * ny) * d.ts;
+    const float* wv = wsl + (size_t)v * ny * d.warea;
 
-    // taps (zero-padded to P, centred) of plane j into buffer b
-    auto prepare = [&](int j, int b) {
-        float* FX = TAP + b * 2 * PT;
-        for (int a = tid; a < PT; a += T) {
-            const int ax = a - ox, az = a - oz;
-            FX[a] = (ax >= 0 && ax < g.px) ? __ldg(fx + ((size_t)lp * ny + j) * g.px + ax) : 0.f;
-            FX[PT + a] = (az >= 0 && az < g.pz) ? __ldg(fz + ((size_t)lp * ny + j) * g.pz + az) : 0.f;
-        }
-    };
-    // attenuation plane and rotation table of plane j, one bulk transaction
-    auto fetch = [&](int j) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                     "r"((unsigned)(d.ps + d.ts) * 4u)
-                     : "memory");
-        tma_copy_1d(MB, mub + (size_t)j * d.ps, (unsigned)d.ps * 4u, bar);
-        tma_copy_1d(MB + d.ps, tab + (size_t)j * d.ts, (unsigned)d.ts * 4u, bar);
-    };
-
+    // taps of every plane of the group (zero-padded to P, centred)
+    for (int e = tid; e < (j_end - j_begin) * PT; e += T) {
+        const int jj = e / PT, a = e - jj * PT, j = j_begin + jj;
+        const int ax = a - ox, az = a - oz;
+        TAP[jj * 2 * PT + a] = (ax >= 0 && ax < g.px) ? __ldg(fx + ((size_t)lp * ny + j) * g.px + ax) : 0.f;
+        TAP[jj * 2 * PT + PT + a] = (az >= 0 && az < g.pz) ? __ldg(fz + ((size_t)lp * ny + j) * g.pz + az) : 0.f;
+    }
     for (int e = tid; e < nx * d.apc; e += T) ACC[e] = 0.f;
-    prepare(j_begin, 0);
     if (tid == 0) {
         mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        fetch(j_begin);
+        tma_load_1d(WB, wv + (size_t)j_begin * d.warea, (unsigned)d.warea * 4u, bar);
+        if (j_begin + 1 < j_end)
+            tma_load_1d(WB + d.warea, wv + (size_t)(j_begin + 1) * d.warea, (unsigned)d.warea * 4u, bar + 1);
     }
     __syncthreads();
 
-    unsigned phase = 0;
+    unsigned phase[2] = {0u, 0u};
     for (int j = j_begin; j < j_end; ++j) {
         const int b = (j - j_begin) & 1;
-        const float* FX = TAP + b * 2 * PT;
+        const float* FX = TAP + (j - j_begin) * 2 * PT;
         const float* FZ = FX + PT;
-
-        // rotate + attenuate the plane into W[k][C+i]: a warp per pair of
-        // rows i, lanes over k (up to 128 k per pass), so the table entry and
-        // the four corner pointers are warp-uniform and 32 gathers per warp
-        // are in flight; replicate halo columns come from the first/last row
-        const bool ok = mbar_wait_bounded(bar, phase);
-        phase ^= 1u;
-        if (ok) {
-            for (int i = 2 * warp; i < nx; i += 2 * NW) {
-                const bool two = i + 1 < nx;
-                const float4 wa = TW[i];
-                const float4 wb = two ? TW[i + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float* pa = xt + (size_t)TB[i] * nz;
-                const float* pb = xt + (size_t)(two ? TB[i + 1] : TB[i]) * nz;
-                for (int k0 = 0; k0 < nz; k0 += 128) {
-                    float xa[4][4], xb[4][4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int k = k0 + 32 * q + lane;
-                        if (k < nz) {
-                            xa[q][0] = __ldg(pa + k);
-                            xa[q][1] = __ldg(pa + nz + k);
-                            xa[q][2] = __ldg(pa + pln + k);
-                            xa[q][3] = __ldg(pa + pln + nz + k);
-                            xb[q][0] = __ldg(pb + k);
-                            xb[q][1] = __ldg(pb + nz + k);
-                            xb[q][2] = __ldg(pb + pln + k);
-                            xb[q][3] = __ldg(pb + pln + nz + k);
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int k = k0 + 32 * q + lane;
-                        if (k < nz) {
-                            float* wr = W + k * d.wp + C;
-                            float va = wa.x * xa[q][0];
-                            va = fmaf(wa.y, xa[q][1], va);
-                            va = fmaf(wa.z, xa[q][2], va);
-                            va = fmaf(wa.w, xa[q][3], va);
-                            va *= MB[i * nz + k];
-                            wr[i] = va;
-                            if (two) {
-                                float vb = wb.x * xb[q][0];
-                                vb = fmaf(wb.y, xb[q][1], vb);
-                                vb = fmaf(wb.z, xb[q][2], vb);
-                                vb = fmaf(wb.w, xb[q][3], vb);
-                                vb *= MB[(i + 1) * nz + k];
-                                wr[i + 1] = vb;
-                                if (i + 1 == nx - 1)
-                                    for (int h = nx; h < wcols - C; ++h) wr[h] = vb;
-                            }
-                            if (i == 0)
-                                for (int h = -C; h < 0; ++h) wr[h] = va;
-                            if (i == nx - 1)
-                                for (int h = nx; h < wcols - C; ++h) wr[h] = va;
-                        }
-                    }
-                }
-            }
-        }
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                flag_timeout(err);
-                mbar_wait_bounded(bar, phase ^ 1u);  // give the copy in flight a last chance to land
-            }
-            return;
-        }
-        // MB and the table are free again: bring in the next plane's
-        if (tid == 0 && j + 1 < j_end) {
-            fence_proxy_async_smem();
-            fetch(j + 1);
-        }
+        const float* W = WB + b * (size_t)d.warea;
+        const bool ok = mbar_wait_bounded(bar + b, phase[b]);
+        phase[b] ^= 1u;
 
         // i-pass: U(i,k) = sum_a fx(a) w(clamp(i-a+cx), k); lanes over k.  The
-        // replicate halo columns of U are written by the warp holding k = 0 or
+        // replicate halo columns of U are written by the warps holding k = 0 or
         // k = nz-1, one lane per column, from shuffled values.
         const int nxi = nz * d.nib;
         for (int base = 0; base < nxi; base += T) {
             const int it = base + tid;
-            const bool valid = it < nxi;
+            const bool valid = ok && it < nxi;
             const int ib = valid ? it / nz : 0, k = valid ? it - ib * nz : 0;
             const int i0 = ib * CX;
             float o[CX];
@@ -474,11 +487,21 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
                 }
             }
         }
-        __syncthreads();
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                flag_timeout(err);
+                mbar_wait_bounded(bar + b, phase[b] ^ 1u);  // give the copies in flight a last chance to land
+                mbar_wait_bounded(bar + (b ^ 1), phase[b ^ 1]);
+            }
+            return;
+        }
+        // buffer b has been read: request plane j+2 into it
+        if (tid == 0 && j + 2 < j_end) {
+            fence_proxy_async_smem();
+            tma_load_1d(WB + b * (size_t)d.warea, wv + (size_t)(j + 2) * d.warea, (unsigned)d.warea * 4u, bar + b);
+        }
 
-        // next plane's taps and table (other buffer), then the k-pass into the
-        // depth-sum accumulators: lanes over i
-        if (j + 1 < j_end) prepare(j + 1, b ^ 1);
+        // k-pass into the depth-sum accumulators: lanes over i
         for (int it = tid; it < nx * d.nkb; it += T) {
             const int kb = it / nx, i = it - kb * nx;
             float win[WZ];
@@ -547,8 +570,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
     float* Zb = sm;
     float* V = Zb + d.warea;
     float* MB = V + (size_t)nx * d.kpu;  // [2][ps]
-    float* TAP = MB + 2 * (size_t)d.ps;  // [2][FX 3 classes | FZ 3 classes] x PT
-    uint64_t* bar = reinterpret_cast<uint64_t*>(TAP + 12 * PT);
+    float* TAP = MB + 2 * (size_t)d.ps;  // [J][FX 3 classes | FZ 3 classes] x PT, every plane of the group
+    uint64_t* bar = reinterpret_cast<uint64_t*>(TAP + 6 * PT * (size_t)d.J);
     const int tid = threadIdx.x;
     constexpr int T = kFusedThreads;
     const int grp = blockIdx.x, v = blockIdx.y, l = l0 + v;
@@ -560,17 +583,16 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
     const float* mub = mubar + ((size_t)l * ny) * d.ps;
     float* tsl = slab + ((size_t)v * ny) * d.ps;
 
-    auto prepare = [&](int j, int b) {
-        float* F = TAP + b * 6 * PT;
-        for (int e = tid; e < 3 * PT; e += T) {
-            const int c = e / PT, a = e - c * PT;
-            const int ax = a - ox, az = a - oz;
-            F[e] = (ax >= 0 && ax < g.px) ? __ldg(fx_adj + ((size_t)c * nrow + (size_t)lp * ny + j) * g.px + ax) : 0.f;
-            F[3 * PT + e] = (c < cls_z && az >= 0 && az < g.pz)
-                                ? __ldg(fz_adj + ((size_t)c * nrow + (size_t)lp * ny + j) * g.pz + az)
-                                : 0.f;
-        }
-    };
+    // edge-class taps of every plane of the group
+    for (int e = tid; e < (j_end - j_begin) * 3 * PT; e += T) {
+        const int jj = e / (3 * PT), r3 = e - jj * 3 * PT, c = r3 / PT, a = r3 - c * PT, j = j_begin + jj;
+        const int ax = a - ox, az = a - oz;
+        float* F = TAP + jj * 6 * PT;
+        F[r3] = (ax >= 0 && ax < g.px) ? __ldg(fx_adj + ((size_t)c * nrow + (size_t)lp * ny + j) * g.px + ax) : 0.f;
+        F[3 * PT + r3] = (c < cls_z && az >= 0 && az < g.pz)
+                             ? __ldg(fz_adj + ((size_t)c * nrow + (size_t)lp * ny + j) * g.pz + az)
+                             : 0.f;
+    }
 
     // stage the detector plane v(:,:,l) transposed, zero outside the detector
     for (int e = tid; e < nx * d.kpu; e += T) V[e] = 0.f;
@@ -581,7 +603,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         tma_load_1d(MB, mub + (size_t)j_begin * d.ps, (unsigned)d.ps * 4u, bar);
     }
-    prepare(j_begin, 0);
     __syncthreads();
     for (int e = tid; e < pln; e += T) {
         const int k = e / nx, i = e - k * nx;
@@ -592,16 +613,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
     unsigned phase[2] = {0u, 0u};
     for (int j = j_begin; j < j_end; ++j) {
         const int n = j - j_begin, b = n & 1;
-        const float* FX = TAP + b * 6 * PT;
+        const float* FX = TAP + n * 6 * PT;
         const float* FZ = FX + 3 * PT;
-        // the other buffer: once the previous plane's bulk store has read it,
-        // it receives the next plane's attenuation
-        if (tid == 0 && j + 1 < j_end) {
-            tma_store_wait_read<0>();
-            tma_load_1d(MB + (b ^ 1) * (size_t)d.ps, mub + (size_t)(j + 1) * d.ps, (unsigned)d.ps * 4u, bar + (b ^ 1));
-        }
-        if (j + 1 < j_end) prepare(j + 1, b ^ 1);
-
         // k-adjoint: Zb[k][C+i] = sum_b' fz~(b') v(i, k+b'-cz), lanes over i
         for (int it = tid; it < nx * d.nkb; it += T) {
             const int kb = it / nx, i = it - kb * nx;
@@ -628,6 +641,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
                 if (k0 + c < nz) Zb[(k0 + c) * d.wp + C + i] = o[c];
         }
         __syncthreads();
+        // the other buffer: the previous plane's bulk store has had the whole
+        // k-adjoint to read it; it now receives the next plane's attenuation
+        if (tid == 0 && j + 1 < j_end) {
+            tma_store_wait_read<0>();
+            tma_load_1d(MB + (b ^ 1) * (size_t)d.ps, mub + (size_t)(j + 1) * d.ps, (unsigned)d.ps * 4u, bar + (b ^ 1));
+        }
 
         // i-adjoint times mubar, in place in MB[b]; lanes over k
         float* mb = MB + b * (size_t)d.ps;
@@ -715,7 +734,39 @@ __global__ void __launch_bounds__(256) k_adj_rot_t(Geometry g, int ps, const Adj
     const float* t = slab + k;
     const size_t vstride = (size_t)g.ny * ps;
     KSum acc[VEC];
-    for (int v = 0; v < nv; ++v) {
+    // four views per step: all entry loads, then all slab loads, are issued
+    // before any is used, so the chain of dependent loads is 4x shorter
+    constexpr int UV = 4;
+    int v = 0;
+    for (; v + UV <= nv; v += UV) {
+        AdjEntry a[UV][MAXE];
+#pragma unroll
+        for (int w = 0; w < UV; ++w)
+#pragma unroll
+            for (int m = 0; m < MAXE; ++m) a[w][m] = e[w * MAXE + m];
+        VT tv[UV][MAXE];
+#pragma unroll
+        for (int w = 0; w < UV; ++w)
+#pragma unroll
+            for (int m = 0; m < MAXE; ++m) tv[w][m] = *reinterpret_cast<const VT*>(t + w * vstride + a[w][m].p);
+#pragma unroll
+        for (int w = 0; w < UV; ++w) {
+            float sv[VEC];
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) sv[u] = 0.f;
+#pragma unroll
+            for (int m = 0; m < MAXE; ++m) {
+                const float* tf = reinterpret_cast<const float*>(&tv[w][m]);
+#pragma unroll
+                for (int u = 0; u < VEC; ++u) sv[u] = fmaf(a[w][m].w, tf[u], sv[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) acc[u].add(sv[u]);
+        }
+        e += UV * MAXE;
+        t += UV * vstride;
+    }
+    for (; v < nv; ++v) {
         AdjEntry a[MAXE];
 #pragma unroll
         for (int m = 0; m < MAXE; ++m) a[m] = e[m];
@@ -805,8 +856,19 @@ cudaError_t fwd_launch(const spect_plan_s& Pl, const float* xt, int l0, int nv, 
     const size_t smem = smem_fwd<P>(Pl.g, d);
     cudaError_t e = cudaFuncSetAttribute(k_fwd_sep_fused<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_fwd_sep_fused<P><<<dim3(d.G, nv), kFusedThreads, smem, st>>>(Pl.g, d, Pl.rtab, xt, Pl.mubar, Pl.fx, Pl.fz,
-                                                                    Pl.part, l0, Pl.err);
+    k_fwd_sep_fused<P><<<dim3(d.G, nv), kFusedThreads, smem, st>>>(Pl.g, d, Pl.slab, Pl.fx, Pl.fz, Pl.part, l0,
+                                                                    Pl.err);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t rot_launch(const spect_plan_s& Pl, const float* xt, int l0, int nv, cudaStream_t st)
+{
+    const FusedDims d = dims_for<P>(Pl.g, Pl.fused_J);
+    const size_t smem = (size_t)d.warea * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_rot_fwd<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_rot_fwd<P><<<dim3(Pl.g.ny, nv), kRotThreads, smem, st>>>(Pl.g, d, Pl.rtab, xt, Pl.mubar, Pl.slab, l0);
     return cudaGetLastError();
 }
 
@@ -865,6 +927,23 @@ int fused_groups(const spect_plan_s& P) { return (P.g.ny + P.fused_J - 1) / P.fu
 cudaError_t launch_fused_forward(const spect_plan_s& P, const float* xt, int l0, int nv, cudaStream_t st)
 {
     SPECT_DISPATCH(fwd_launch, P, xt, l0, nv, st)
+}
+
+cudaError_t launch_fused_rotate(const spect_plan_s& P, const float* xt, int l0, int nv, cudaStream_t st)
+{
+    SPECT_DISPATCH(rot_launch, P, xt, l0, nv, st)
+}
+
+// floats per view of the work slab the fused path needs (rotated planes or t planes)
+size_t fused_slab_per_view(const spect_plan_s& P)
+{
+    const int p = P.bucket;
+    int C = (p - 1) / 2;
+    const int nib = (P.g.nx + 15) / 16;
+    const int wp = (nib * 16 + 2 * C) | 1;
+    const size_t warea = ((size_t)P.g.nz * wp + 3) & ~(size_t)3;
+    const size_t ps = ((size_t)P.g.nx * P.g.nz + 3) & ~(size_t)3;
+    return (size_t)P.g.ny * (warea > ps ? warea : ps);
 }
 
 cudaError_t launch_fused_adjoint(const spect_plan_s& P, const float* v, int l0, int nv, cudaStream_t st)

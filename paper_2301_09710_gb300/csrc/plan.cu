@@ -222,9 +222,16 @@ spect_status from_internal(spect_plan_s* P, const float* xt, float* x, cudaStrea
 spect_status fast_forward(spect_plan_s* P, const float* xt, float* v, const float* y, const float* rbar,
                           cudaStream_t st)
 {
-    SPECT_CUDA_TRY(counted(P, SPECT_K_CONV_FWD, st,
-                           [&] { return spect::launch_fused_forward(*P, xt, 0, P->g.nview, st); }),
-                   "fused forward launch");
+    const int nview = P->g.nview;
+    for (int l0 = 0; l0 < nview; l0 += P->chunk) {
+        const int nv = std::min(P->chunk, nview - l0);
+        SPECT_CUDA_TRY(counted(P, SPECT_K_ROTATE_ATTEN, st,
+                               [&] { return spect::launch_fused_rotate(*P, xt, l0, nv, st); }),
+                       "rotation launch");
+        SPECT_CUDA_TRY(counted(P, SPECT_K_CONV_FWD, st,
+                               [&] { return spect::launch_fused_forward(*P, xt, l0, nv, st); }),
+                       "fused forward launch");
+    }
     SPECT_CUDA_TRY(counted(P, SPECT_K_OTHER, st, [&] { return spect::launch_fwd_reduce(*P, v, y, rbar, st); }),
                    "depth-group reduce launch");
     return SPECT_OK;
@@ -455,7 +462,8 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
 
     // work slab and EM buffers
     const size_t budget = slab_budget_bytes(P->fast);
-    const size_t per_view = std::max(vol, (size_t)ny * P->ps);  // fused path pads planes to ps floats
+    // the fused path stores padded planes (rotated image planes or adjoint planes)
+    const size_t per_view = std::max(vol, P->fast ? spect::fused_slab_per_view(*P) : vol);
     P->chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)nview, budget / (per_view * sizeof(float))));
     PLAN_ALLOC(P->slab, per_view * (size_t)P->chunk, "work slab");
     PLAN_ALLOC(P->e, vol, "EM accumulator");

@@ -279,6 +279,8 @@ cudaError_t launch_mubar_cache(const spect_plan_s& P, const float* mu_t, cudaStr
 cudaError_t launch_build_adjacency_fixed(const spect_plan_s& P, cudaStream_t st);
 cudaError_t launch_rot_tables(const spect_plan_s& P, cudaStream_t st);
 cudaError_t launch_fused_forward(const spect_plan_s& P, const float* xt, int l0, int nv, cudaStream_t st);
+cudaError_t launch_fused_rotate(const spect_plan_s& P, const float* xt, int l0, int nv, cudaStream_t st);
+size_t fused_slab_per_view(const spect_plan_s& P);
 cudaError_t launch_fused_adjoint(const spect_plan_s& P, const float* v, int l0, int nv, cudaStream_t st);
 cudaError_t launch_fwd_reduce(const spect_plan_s& P, float* v, const float* em_y, const float* em_rbar,
                               cudaStream_t st);
