@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
     float* TAP = U + (size_t)nx * d.kpu;               // [J][FX PT | FZ PT], every plane of the group
     float* ACC = TAP + 2 * PT * (size_t)d.J;           // nx x apc, [i][k]
     uint64_t* bar = reinterpret_cast<uint64_t*>(ACC + (size_t)nx * d.apc);
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x;
     constexpr int T = kFusedThreads;
     const int grp = blockIdx.x, v = blockIdx.y, l = l0 + v;
     const int lp = g.nvp == 1 ? 0 : l;
@@ -437,21 +437,16 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
         const bool ok = mbar_wait_bounded(bar + b, phase[b]);
         phase[b] ^= 1u;
 
-        // i-pass: U(i,k) = sum_a fx(a) w(clamp(i-a+cx), k); lanes over k.  The
-        // replicate halo columns of U are written by the warps holding k = 0 or
-        // k = nz-1, one lane per column, from shuffled values.
-        const int nxi = nz * d.nib;
-        for (int base = 0; base < nxi; base += T) {
-            const int it = base + tid;
-            const bool valid = ok && it < nxi;
-            const int ib = valid ? it / nz : 0, k = valid ? it - ib * nz : 0;
-            const int i0 = ib * CX;
-            float o[CX];
-            if (valid) {
+        // i-pass: U(i,k) = sum_a fx(a) w(clamp(i-a+cx), k); lanes over k
+        if (ok) {
+            for (int it = tid; it < nz * d.nib; it += T) {
+                const int ib = it / nz, k = it - ib * nz;
+                const int i0 = ib * CX;
                 const float* wr = W + k * d.wp + i0;
                 float win[CX + P - 1];
 #pragma unroll
                 for (int m = 0; m < CX + P - 1; ++m) win[m] = wr[m];
+                float o[CX];
                 fir<P, CX, -1, P - 1>(FX, win, o);
                 float* ur = U + i0 * d.kpu + ZH + k;
                 if (i0 + CX <= nx) {
@@ -461,29 +456,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
 #pragma unroll
                     for (int c = 0; c < CX; ++c)
                         if (i0 + c < nx) ur[c * d.kpu] = o[c];
-                }
-            }
-            const unsigned m0 = __ballot_sync(0xffffffffu, valid && k == 0);
-            const unsigned m1 = __ballot_sync(0xffffffffu, valid && k == nz - 1);
-            for (unsigned mm = m0; mm; mm &= mm - 1) {  // every lane of this warp holding k = 0
-                const int src = __ffs(mm) - 1;
-                const int i0s = __shfl_sync(0xffffffffu, i0, src);
-#pragma unroll
-                for (int c = 0; c < CX; ++c) {
-                    const float vv = __shfl_sync(0xffffffffu, o[c], src);
-                    if (i0s + c < nx)
-                        for (int h = lane; h < ZH; h += 32) U[(i0s + c) * d.kpu + h] = vv;
-                }
-            }
-            for (unsigned mm = m1; mm; mm &= mm - 1) {  // every lane holding k = nz-1
-                const int src = __ffs(mm) - 1;
-                const int i0s = __shfl_sync(0xffffffffu, i0, src);
-                const int nr = d.kpu - ZH - nz;
-#pragma unroll
-                for (int c = 0; c < CX; ++c) {
-                    const float vv = __shfl_sync(0xffffffffu, o[c], src);
-                    if (i0s + c < nx)
-                        for (int h = lane; h < nr; h += 32) U[(i0s + c) * d.kpu + ZH + nz + h] = vv;
                 }
             }
         }
@@ -501,11 +473,22 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
             tma_load_1d(WB + b * (size_t)d.warea, wv + (size_t)(j + 2) * d.warea, (unsigned)d.warea * 4u, bar + b);
         }
 
-        // k-pass into the depth-sum accumulators: lanes over i
+        // k-pass into the depth-sum accumulators: lanes over i.  The thread of
+        // the first (last) k-block of row i first writes that row's replicate
+        // halo columns, which only it reads.
         for (int it = tid; it < nx * d.nkb; it += T) {
             const int kb = it / nx, i = it - kb * nx;
+            float* ur = U + i * d.kpu;
+            if (kb == 0) {
+                const float lo = ur[ZH];
+                for (int h = 0; h < ZH; ++h) ur[h] = lo;
+            }
+            if (kb == d.nkb - 1) {
+                const float hi = ur[ZH + nz - 1];
+                for (int h = ZH + nz; h < d.kpu; ++h) ur[h] = hi;
+            }
             float win[WZ];
-            load_window_f4<P>(U + i * d.kpu + kb * CZ, win);
+            load_window_f4<P>(ur + kb * CZ, win);
             float o[CZ];
             fir<P, CZ, -1, C + ZH>(FZ, win, o);
             float4* acc4 = reinterpret_cast<float4*>(ACC + i * d.apc + kb * CZ);
@@ -615,30 +598,41 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
         const int n = j - j_begin, b = n & 1;
         const float* FX = TAP + n * 6 * PT;
         const float* FZ = FX + 3 * PT;
-        // k-adjoint: Zb[k][C+i] = sum_b' fz~(b') v(i, k+b'-cz), lanes over i
+        // k-adjoint: Zb[k][C+i] = sum_b' fz~(b') v(i, k+b'-cz), lanes over i.
+        // The first and last detector rows, where replicate padding folds
+        // taps together, take their edge-class taps instead of the interior ones.
         for (int it = tid; it < nx * d.nkb; it += T) {
             const int kb = it / nx, i = it - kb * nx;
+            const float* vr = V + i * d.kpu;
             float win[WZ];
-            load_window_f4<P>(V + i * d.kpu + kb * CZ, win);
+            load_window_f4<P>(vr + kb * CZ, win);
             float o[CZ];
             fir<P, CZ, 1, ZH - C>(FZ, win, o);
             const int k0 = kb * CZ;
-            if (nz > 1 && (k0 == 0 || k0 + CZ > nz - 1)) {  // replicate-padding folds on the first/last rows
+            if (nz > 1 && k0 == 0) {  // row k = 0
+                const float* f = FZ + PT;
+                float sacc = 0.f;
 #pragma unroll
-                for (int c = 0; c < CZ; ++c) {
-                    const int k = k0 + c;
-                    if (k == 0 || k == nz - 1) {
-                        const float* f = FZ + (k == 0 ? 1 : 2) * PT;
-                        float sacc = 0.f;
-#pragma unroll
-                        for (int bb = 0; bb < P; ++bb) sacc = fmaf(f[bb], win[c + bb - C + ZH], sacc);
-                        o[c] = sacc;
-                    }
-                }
+                for (int bb = 0; bb < P; ++bb) sacc = fmaf(f[bb], win[bb - C + ZH], sacc);
+                o[0] = sacc;
             }
+            const int cl = nz - 1 - k0;  // position of row k = nz-1 in this block
+            const bool last = nz > 1 && cl < CZ;
+            float e_last = 0.f;
+            if (last) {
+                const float* f = FZ + 2 * PT;
+                const float* vv = vr + (nz - 1) - C + ZH;
+                for (int bb = 0; bb < P; ++bb) e_last = fmaf(f[bb], vv[bb], e_last);
+            }
+            float* zc = Zb + C + i;
+            if (k0 + CZ <= nz && !last) {
 #pragma unroll
-            for (int c = 0; c < CZ; ++c)
-                if (k0 + c < nz) Zb[(k0 + c) * d.wp + C + i] = o[c];
+                for (int c = 0; c < CZ; ++c) zc[(k0 + c) * d.wp] = o[c];
+            } else {
+#pragma unroll
+                for (int c = 0; c < CZ; ++c)
+                    if (k0 + c < nz) zc[(k0 + c) * d.wp] = (last && c == cl) ? e_last : o[c];
+            }
         }
         __syncthreads();
         // the other buffer: the previous plane's bulk store has had the whole
@@ -662,25 +656,30 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
                 for (int m = 0; m < CX + P - 1; ++m) win[m] = zr[m];
                 float o[CX];
                 fir<P, CX, 1, 0>(FX, win, o);
-                if (i0 == 0 || i0 + CX > nx - 1) {
+                // first / last detector column: edge-class taps (replicate-padding folds)
+                if (i0 == 0) {
+                    const float* f = FX + PT;
+                    float sacc = 0.f;
 #pragma unroll
-                    for (int c = 0; c < CX; ++c) {
-                        const int i = i0 + c;
-                        if (i == 0 || i == nx - 1) {
-                            const float* f = FX + (i == 0 ? 1 : 2) * PT;
-                            float sacc = 0.f;
-#pragma unroll
-                            for (int a = 0; a < P; ++a) sacc = fmaf(f[a], win[c + a], sacc);
-                            o[c] = sacc;
-                        }
-                    }
+                    for (int a = 0; a < P; ++a) sacc = fmaf(f[a], win[a], sacc);
+                    o[0] = sacc;
                 }
+                const int cl = nx - 1 - i0;  // position of column nx-1 in this block
+                const bool last = cl < CX;
+                float e_last = 0.f;
+                if (last) {
+                    const float* f = FX + 2 * PT;
+                    for (int a = 0; a < P; ++a) e_last = fmaf(f[a], zr[cl + a], e_last);
+                }
+                float* mp = mb + i0 * nz + k;
+                if (!last) {
 #pragma unroll
-                for (int c = 0; c < CX; ++c)
-                    if (i0 + c < nx) {
-                        float* mp = mb + (i0 + c) * nz + k;
-                        *mp = o[c] * *mp;
-                    }
+                    for (int c = 0; c < CX; ++c) mp[c * nz] = o[c] * mp[c * nz];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < CX; ++c)
+                        if (c <= cl) mp[c * nz] = (c == cl ? e_last : o[c]) * mp[c * nz];
+                }
             }
         }
         if (__syncthreads_or(!ok)) {
