@@ -200,10 +200,11 @@ cudaError_t launch_build_adjacency_fixed(const spect_plan_s& P, cudaStream_t st)
 //   W   two plane buffers, nz rows x wp columns: W[k][C + i] with replicate
 //       halo columns; wp is odd so the i-pass windows (lanes over k) are
 //       bank-conflict free and every window load is an immediate offset.
-//   U   nx rows x kpu: i-pass output, U[i][ZH + k], with replicate halo
-//       columns; kpu/4 is odd so the k-pass float4 windows (lanes over i) are
-//       bank-conflict free.
-//   taps of every plane of the group, staged once.
+//   U   nx rows x kpu: i-pass output, U[i][ZH + k], with zero halo columns;
+//       kpu/4 is odd so the k-pass float4 windows (lanes over i) are
+//       bank-conflict free.  Replicate padding along k enters as folded edge
+//       taps: output k adds U(0) sum_{b>k+C} fz(b) + U(nz-1) sum_{b<k+C-nz+1} fz(b).
+//   taps and folded edge taps of every plane of the group, staged once.
 //   ACC nx x apc depth-sum accumulators of the group, [i][k] (apc/4 odd, so
 //       the k-pass float4 read-modify-writes are bank-conflict free).
 // Per plane there are two block barriers: after the i-pass (which also agrees
@@ -235,8 +236,9 @@ struct FusedDims {
 
 __host__ __device__ inline size_t fwd_smem_floats(const FusedDims& d, int nx, int nz, int PT)
 {
-    // W x2 | U | taps J x (FX,FZ) | ACC | 2 mbarriers
-    return 2 * (size_t)d.warea + (size_t)nx * d.kpu + 2 * (size_t)PT * d.J + (size_t)nx * d.apc + 8;
+    // W x2 | U | taps J x (FX,FZ) | ACC | folded edge taps J x 2 x nz | 2 mbarriers
+    return 2 * (size_t)d.warea + (size_t)nx * d.kpu + 2 * (size_t)PT * d.J + (size_t)nx * d.apc +
+           2 * (size_t)d.J * nz + 10;
 }
 
 __host__ __device__ inline size_t adj_smem_floats(const FusedDims& d, int nx, int PT)
@@ -400,7 +402,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
     float* U = WB + 2 * (size_t)d.warea;
     float* TAP = U + (size_t)nx * d.kpu;               // [J][FX PT | FZ PT], every plane of the group
     float* ACC = TAP + 2 * PT * (size_t)d.J;           // nx x apc, [i][k]
-    uint64_t* bar = reinterpret_cast<uint64_t*>(ACC + (size_t)nx * d.apc);
+    float* FOLD = ACC + (size_t)nx * d.apc;             // [J][2][nz] folded edge taps of the k-pass
+    uint64_t* bar = reinterpret_cast<uint64_t*>(FOLD + ((2 * (size_t)d.J * nz + 1) & ~(size_t)1));
     const int tid = threadIdx.x;
     constexpr int T = kFusedThreads;
     const int grp = blockIdx.x, v = blockIdx.y, l = l0 + v;
@@ -417,7 +420,25 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
         TAP[jj * 2 * PT + a] = (ax >= 0 && ax < g.px) ? __ldg(fx + ((size_t)lp * ny + j) * g.px + ax) : 0.f;
         TAP[jj * 2 * PT + PT + a] = (az >= 0 && az < g.pz) ? __ldg(fz + ((size_t)lp * ny + j) * g.pz + az) : 0.f;
     }
+    // replicate padding along k, folded: output k takes U(0) * sum_{b > k+C} fz(b)
+    // and U(nz-1) * sum_{b < k+C-nz+1} fz(b) on top of the zero-padded k-pass
+    for (int e = tid; e < (j_end - j_begin) * nz; e += T) {
+        const int jj = e / nz, k = e - jj * nz, j = j_begin + jj;
+        const float* f = fz + ((size_t)lp * ny + j) * g.pz;
+        float lo = 0.f, hi = 0.f;
+        for (int bq = k + C + 1; bq < P; ++bq) {
+            const int az = bq - oz;
+            if (az >= 0 && az < g.pz) lo += __ldg(f + az);
+        }
+        for (int bq = 0; bq < k + C - nz + 1 && bq < P; ++bq) {
+            const int az = bq - oz;
+            if (az >= 0 && az < g.pz) hi += __ldg(f + az);
+        }
+        FOLD[(jj * 2) * nz + k] = lo;
+        FOLD[(jj * 2 + 1) * nz + k] = hi;
+    }
     for (int e = tid; e < nx * d.apc; e += T) ACC[e] = 0.f;
+    for (int e = tid; e < nx * d.kpu; e += T) U[e] = 0.f;  // zero k-halo columns (never written again)
     if (tid == 0) {
         mbar_init(bar, 1);
         mbar_init(bar + 1, 1);
@@ -467,30 +488,33 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
             }
             return;
         }
-        // buffer b has been read: request plane j+2 into it
-        if (tid == 0 && j + 2 < j_end) {
+        // buffer b has been read: request plane j+2 into it (from the last warp,
+        // which has the fewest halo rows below)
+        if (tid == T - 32 && j + 2 < j_end) {
             fence_proxy_async_smem();
             tma_load_1d(WB + b * (size_t)d.warea, wv + (size_t)(j + 2) * d.warea, (unsigned)d.warea * 4u, bar + b);
         }
 
-        // k-pass into the depth-sum accumulators: lanes over i.  The thread of
-        // the first (last) k-block of row i first writes that row's replicate
-        // halo columns, which only it reads.
+        // k-pass into the depth-sum accumulators: lanes over i; zero-padded
+        // FIR plus the folded replicate-padding terms on the edge rows
+        const float* fold_lo = FOLD + (j - j_begin) * 2 * nz;
+        const float* fold_hi = fold_lo + nz;
         for (int it = tid; it < nx * d.nkb; it += T) {
             const int kb = it / nx, i = it - kb * nx;
-            float* ur = U + i * d.kpu;
-            if (kb == 0) {
-                const float lo = ur[ZH];
-                for (int h = 0; h < ZH; ++h) ur[h] = lo;
-            }
-            if (kb == d.nkb - 1) {
-                const float hi = ur[ZH + nz - 1];
-                for (int h = ZH + nz; h < d.kpu; ++h) ur[h] = hi;
-            }
+            const float* ur = U + i * d.kpu;
             float win[WZ];
             load_window_f4<P>(ur + kb * CZ, win);
             float o[CZ];
             fir<P, CZ, -1, C + ZH>(FZ, win, o);
+            const int k0 = kb * CZ;
+            if (k0 < C || k0 + CZ > nz - C) {
+                const float ulo = ur[ZH], uhi = ur[ZH + nz - 1];
+#pragma unroll
+                for (int c = 0; c < CZ; ++c) {
+                    const int k = min(k0 + c, nz - 1);
+                    o[c] = fmaf(ulo, fold_lo[k], fmaf(uhi, fold_hi[k], o[c]));
+                }
+            }
             float4* acc4 = reinterpret_cast<float4*>(ACC + i * d.apc + kb * CZ);
 #pragma unroll
             for (int c4 = 0; c4 < CZ / 4; ++c4) {
