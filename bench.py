@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--direct-steps", type=int, default=3, help="steps of the full-PSF path reported beside (0: skip)")
     ap.add_argument("--cpu-views", type=int, default=0, help="views in the CPU baseline sample (0: auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nview", type=int, default=NVIEW,
+                    help="views of the workload (default 128; fewer only for small profiler captures)")
     return ap.parse_args()
 
 
@@ -102,17 +104,17 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- workload
-def make_workload(device, path):
+def make_workload(device, path, nview=NVIEW):
     import torch
 
     from paper_2301_09710_gb300 import SpectPlan, synthetic
 
-    prob = synthetic.config2(seed=0, nx=NX, nz=NZ, nview=NVIEW, psf_size=PSF)
+    prob = synthetic.config2(seed=0, nx=NX, nz=NZ, nview=nview, psf_size=PSF)
     sep = path == "separable"
     if sep:
-        plan = SpectPlan(NX, NZ, NVIEW, mu=prob.mu, dy=prob.dy, fx=prob.fx, fz=prob.fz, device=device)
+        plan = SpectPlan(NX, NZ, nview, mu=prob.mu, dy=prob.dy, fx=prob.fx, fz=prob.fz, device=device)
     else:
-        plan = SpectPlan(NX, NZ, NVIEW, mu=prob.mu, dy=prob.dy, psf=prob.full_psf(), device=device)
+        plan = SpectPlan(NX, NZ, nview, mu=prob.mu, dy=prob.dy, psf=prob.full_psf(), device=device)
     xt = torch.from_numpy(prob.x).to(device)
     primary = plan.forward(xt)
     scale = 1e7 / float(primary.sum())
@@ -123,7 +125,7 @@ def make_workload(device, path):
     return prob, plan, x0, y, rbar
 
 
-def algorithmic_flops(kind: str, nv: float, sep: bool, fused: bool = False) -> float:
+def algorithmic_flops(kind: str, nv: float, sep: bool, fused: bool = False) -> float:  # noqa: C901
     """Algorithmic FLOPs of one launch of a kernel class that processes nv views.
 
     Per voxel-view: blur 2(px+pz) (separable) or 2 px pz (full PSF); bilinear
@@ -164,7 +166,7 @@ def run_ours(args):
     from __graft_entry__ import build
     build()
 
-    prob, plan, x0_h, y_h, rbar_h = make_workload(device, args.path)
+    prob, plan, x0_h, y_h, rbar_h = make_workload(device, args.path, args.nview)
     info = plan.info()
     sep = info["separable"]
     chunk = info["view_chunk"]
@@ -220,7 +222,7 @@ def run_ours(args):
     for k, (n, ms) in prof.items():
         if n == 0:
             continue
-        nv_avg = NVIEW * args.steps / n if k != "other" else 0
+        nv_avg = args.nview * args.steps / n if k != "other" else 0
         fl = algorithmic_flops(k, nv_avg, sep, info["fused"]) if k != "other" else 0.0
         kern[k] = {"launches": n, "ms_total": ms, "ms_avg": ms / n, "share": None,
                    "tflops": (fl / (ms / n * 1e-3) / 1e12) if ms > 0 and fl else None}
@@ -292,7 +294,7 @@ def run_ours(args):
                "config": {"workload": "128x128x80 image, 128 views over 360 deg, 37x37 depth-dependent "
                                       "anisotropic Gaussian PSF (separable factors), MLEM step with 10% smoothed "
                                       "background, XCAT-like ellipsoid phantom (seed 0)",
-                          "path": args.path, "fused": info["fused"], "view_chunk": chunk, "parallelism": f"replicas{world}",
+                          "path": args.path, "fused": info["fused"], "view_chunk": chunk, "nview": args.nview, "parallelism": f"replicas{world}",
                           "l2": "flushed between timed steps (256 MB write)",
                           "step": "one EM iteration = one A + one A' + fused ratio/update"},
                "clocks": clk.summary(), "gpu_launches": n_launch, "e2e": e2e, "roofline": roofline,

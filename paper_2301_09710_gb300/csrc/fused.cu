@@ -420,23 +420,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
         TAP[jj * 2 * PT + a] = (ax >= 0 && ax < g.px) ? __ldg(fx + ((size_t)lp * ny + j) * g.px + ax) : 0.f;
         TAP[jj * 2 * PT + PT + a] = (az >= 0 && az < g.pz) ? __ldg(fz + ((size_t)lp * ny + j) * g.pz + az) : 0.f;
     }
-    // replicate padding along k, folded: output k takes U(0) * sum_{b > k+C} fz(b)
-    // and U(nz-1) * sum_{b < k+C-nz+1} fz(b) on top of the zero-padded k-pass
-    for (int e = tid; e < (j_end - j_begin) * nz; e += T) {
-        const int jj = e / nz, k = e - jj * nz, j = j_begin + jj;
-        const float* f = fz + ((size_t)lp * ny + j) * g.pz;
-        float lo = 0.f, hi = 0.f;
-        for (int bq = k + C + 1; bq < P; ++bq) {
-            const int az = bq - oz;
-            if (az >= 0 && az < g.pz) lo += __ldg(f + az);
-        }
-        for (int bq = 0; bq < k + C - nz + 1 && bq < P; ++bq) {
-            const int az = bq - oz;
-            if (az >= 0 && az < g.pz) hi += __ldg(f + az);
-        }
-        FOLD[(jj * 2) * nz + k] = lo;
-        FOLD[(jj * 2 + 1) * nz + k] = hi;
-    }
     for (int e = tid; e < nx * d.apc; e += T) ACC[e] = 0.f;
     for (int e = tid; e < nx * d.kpu; e += T) U[e] = 0.f;  // zero k-halo columns (never written again)
     if (tid == 0) {
@@ -446,6 +429,18 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
         tma_load_1d(WB, wv + (size_t)j_begin * d.warea, (unsigned)d.warea * 4u, bar);
         if (j_begin + 1 < j_end)
             tma_load_1d(WB + d.warea, wv + (size_t)(j_begin + 1) * d.warea, (unsigned)d.warea * 4u, bar + 1);
+    }
+    __syncthreads();
+    // replicate padding along k, folded: output k takes U(0) * sum_{b > k+C} fz(b)
+    // and U(nz-1) * sum_{b < k+C-nz+1} fz(b) on top of the zero-padded k-pass
+    for (int e = tid; e < (j_end - j_begin) * nz; e += T) {
+        const int jj = e / nz, k = e - jj * nz;
+        const float* f = TAP + jj * 2 * PT + PT;
+        float lo = 0.f, hi = 0.f;
+        for (int bq = k + C + 1; bq < P; ++bq) lo += f[bq];
+        for (int bq = 0; bq < k + C - nz + 1 && bq < P; ++bq) hi += f[bq];
+        FOLD[(jj * 2) * nz + k] = lo;
+        FOLD[(jj * 2 + 1) * nz + k] = hi;
     }
     __syncthreads();
 
