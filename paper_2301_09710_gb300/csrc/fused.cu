@@ -326,42 +326,20 @@ __global__ void __launch_bounds__(kRotThreads, 2) k_rot_fwd(Geometry g, FusedDim
         const float4 wb = two ? __ldg(TW + i + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float* pa = xt + (size_t)__ldg(TB + i) * nz;
         const float* pb = xt + (size_t)__ldg(TB + (two ? i + 1 : i)) * nz;
-        // corners of row i+1 that coincide with corners of row i are not loaded
-        // again (its base differs by 1, nx or nx+1 for most angles); corners with
-        // zero weight are not loaded at all
-        const int bA = __ldg(TB + i), bB = __ldg(TB + (two ? i + 1 : i));
-        const int off[4] = {0, 1, nx, nx + 1};
-        int dup[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            dup[c] = -1;
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-                if (bB + off[c] == bA + off[a]) dup[c] = a;
-        }
-        const float wav[4] = {wa.x, wa.y, wa.z, wa.w}, wbv[4] = {wb.x, wb.y, wb.z, wb.w};
-        bool reuse[4];  // corner c of row i+1 is a loaded corner of row i
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            reuse[c] = (dup[c] == 0 && wav[0] != 0.f) || (dup[c] == 1 && wav[1] != 0.f) ||
-                       (dup[c] == 2 && wav[2] != 0.f) || (dup[c] == 3 && wav[3] != 0.f);
         for (int k0 = 0; k0 < nz; k0 += 96) {
             float xa[3][4], xb[3][4], ma[3], mc[3];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const int k = k0 + 32 * q + lane;
                 if (k < nz) {
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const size_t o = (size_t)(c < 2 ? 0 : pln) + (c & 1 ? nz : 0) + k;
-                        xa[q][c] = wav[c] != 0.f ? __ldg(pa + o) : 0.f;
-                    }
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const size_t o = (size_t)(c < 2 ? 0 : pln) + (c & 1 ? nz : 0) + k;
-                        const float sel = dup[c] == 0 ? xa[q][0] : dup[c] == 1 ? xa[q][1] : dup[c] == 2 ? xa[q][2] : xa[q][3];
-                        xb[q][c] = (two && wbv[c] != 0.f) ? (reuse[c] ? sel : __ldg(pb + o)) : 0.f;
-                    }
+                    xa[q][0] = __ldg(pa + k);
+                    xa[q][1] = __ldg(pa + nz + k);
+                    xa[q][2] = __ldg(pa + pln + k);
+                    xa[q][3] = __ldg(pa + pln + nz + k);
+                    xb[q][0] = __ldg(pb + k);
+                    xb[q][1] = __ldg(pb + nz + k);
+                    xb[q][2] = __ldg(pb + pln + k);
+                    xb[q][3] = __ldg(pb + pln + nz + k);
                     ma[q] = __ldg(mb + i * nz + k);
                     mc[q] = two ? __ldg(mb + (i + 1) * nz + k) : 0.f;
                 }
