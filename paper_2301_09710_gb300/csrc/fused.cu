@@ -900,7 +900,7 @@ cudaError_t rot_launch(const spect_plan_s& Pl, const float* xt, int l0, int nv, 
 template <int P>
 cudaError_t adj_launch(const spect_plan_s& Pl, const float* v, int l0, int nv, cudaStream_t st)
 {
-    const FusedDims d = dims_for<P>(Pl.g, Pl.fused_J);
+    const FusedDims d = dims_for<P>(Pl.g, Pl.adj_J);
     const size_t smem = smem_adj<P>(Pl.g, d);
     cudaError_t e = cudaFuncSetAttribute(k_adj_sep_fused<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

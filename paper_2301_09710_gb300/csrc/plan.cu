@@ -242,8 +242,8 @@ spect_status fast_back(spect_plan_s* P, const float* v, float* out_t, float* em_
                        cudaStream_t st)
 {
     const int nview = P->g.nview;
-    for (int l0 = 0; l0 < nview; l0 += P->chunk) {
-        const int nv = std::min(P->chunk, nview - l0);
+    for (int l0 = 0; l0 < nview; l0 += P->adj_chunk) {
+        const int nv = std::min(P->adj_chunk, nview - l0);
         const bool last = l0 + nv >= nview;
         SPECT_CUDA_TRY(counted(P, SPECT_K_CONV_ADJ, st, [&] { return spect::launch_fused_adjoint(*P, v, l0, nv, st); }),
                        "fused adjoint launch");
@@ -466,6 +466,21 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
     const size_t per_view = std::max(vol, P->fast ? spect::fused_slab_per_view(*P) : vol);
     P->chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)nview, budget / (per_view * sizeof(float))));
     PLAN_ALLOC(P->slab, per_view * (size_t)P->chunk, "work slab");
+    // fused adjoint: views per pass chosen so the t planes of a pass (ny*ps
+    // floats per view) stay resident in L2 for the gather that follows, and a
+    // depth-group size that still gives about two blocks per SM per pass;
+    // SPECT_ADJ_CHUNK overrides (tuning)
+    {
+        const size_t tview = (size_t)ny * P->ps * sizeof(float);
+        int ac = (int)std::max<size_t>(1, ((size_t)80 << 20) / tview);
+        const char* env = getenv("SPECT_ADJ_CHUNK");
+        if (env && atoi(env) > 0) ac = atoi(env);
+        P->adj_chunk = std::min(std::min(ac, nview), P->chunk);
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int want_groups = std::max(1, (2 * std::max(sms, 1) + P->adj_chunk - 1) / P->adj_chunk);
+        P->adj_J = std::max(1, std::min(8, (ny + want_groups - 1) / want_groups));
+    }
     PLAN_ALLOC(P->e, vol, "EM accumulator");
     PLAN_ALLOC(P->ratio, nproj, "EM ratio");
     PLAN_ALLOC(P->s, vol, "sensitivity");

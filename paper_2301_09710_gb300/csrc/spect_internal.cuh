@@ -76,7 +76,9 @@ struct spect_plan_s {
     // fast path (fused kernels, k-fastest internal layout, cached attenuation)
     int fast = 0;                // 1 when the fused kernels serve this plan
     int bucket = 0;              // padded tap count of the fused kernels
-    int fused_J = 8;             // depth planes per fused block
+    int fused_J = 8;             // depth planes per fused forward block
+    int adj_J = 8;               // depth planes per fused adjoint block
+    int adj_chunk = 0;           // views per adjoint pass (t slab sized to stay in L2)
     float* mubar = nullptr;      // nview * ny*nx*nz, [l][j][i][k]
     float* xt = nullptr;         // nx*ny*nz, [j][i][k] image
     float* et = nullptr;         // nx*ny*nz, [j][i][k] back-projection accumulator
