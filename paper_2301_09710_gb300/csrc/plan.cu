@@ -466,20 +466,19 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
     const size_t per_view = std::max(vol, P->fast ? spect::fused_slab_per_view(*P) : vol);
     P->chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)nview, budget / (per_view * sizeof(float))));
     PLAN_ALLOC(P->slab, per_view * (size_t)P->chunk, "work slab");
-    // fused adjoint: views per pass chosen so the t planes of a pass (ny*ps
-    // floats per view) stay resident in L2 for the gather that follows, and a
-    // depth-group size that still gives about two blocks per SM per pass;
-    // SPECT_ADJ_CHUNK overrides (tuning)
-    {
-        const size_t tview = (size_t)ny * P->ps * sizeof(float);
-        int ac = (int)std::max<size_t>(1, ((size_t)80 << 20) / tview);
-        const char* env = getenv("SPECT_ADJ_CHUNK");
-        if (env && atoi(env) > 0) ac = atoi(env);
-        P->adj_chunk = std::min(std::min(ac, nview), P->chunk);
-        int sms = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int want_groups = std::max(1, (2 * std::max(sms, 1) + P->adj_chunk - 1) / P->adj_chunk);
-        P->adj_J = std::max(1, std::min(8, (ny + want_groups - 1) / want_groups));
+    // fused adjoint: all views of the slab in one pass by default (measured
+    // faster than L2-sized passes); SPECT_ADJ_CHUNK sets fewer views per pass,
+    // with a depth-group size that keeps about two blocks per SM (tuning)
+    P->adj_chunk = P->chunk;
+    P->adj_J = 8;
+    if (const char* env = getenv("SPECT_ADJ_CHUNK")) {
+        if (atoi(env) > 0) {
+            P->adj_chunk = std::min(std::min(atoi(env), nview), P->chunk);
+            int sms = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const int want_groups = std::max(1, (2 * std::max(sms, 1) + P->adj_chunk - 1) / P->adj_chunk);
+            P->adj_J = std::max(1, std::min(8, (ny + want_groups - 1) / want_groups));
+        }
     }
     PLAN_ALLOC(P->e, vol, "EM accumulator");
     PLAN_ALLOC(P->ratio, nproj, "EM ratio");
