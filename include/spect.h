@@ -154,6 +154,21 @@ spect_status spect_em_step(spect_plan plan, float* x, const float* y, const floa
                            int niter, spect_stream stream);
 
 /*
+ * spect_em_step_reg -- niter inner iterations of the regularised EM update,
+ * Eqs. (7)-(8):  x <- (-d + sqrt(d^2 + 4 beta x e)) / (2 beta),
+ * d = A'1 - beta u, e = A'(y / (A x + rbar)); the non-negative root of the EM
+ * surrogate of Eq. (6) with the penalty (beta/2)||x - u||^2.  beta = 0 is the
+ * MLEM update of spect_em_step.
+ *   u     device, nx*ny*nz regulariser target (u = g_theta(x_k) of Eq. (6)),
+ *         read only; may be NULL when beta == 0.
+ *   beta  >= 0.
+ * The root is evaluated in the cancellation-free form for the sign of d.
+ * Errors as spect_em_step; SPECT_EINVAL for beta < 0 or u missing.
+ */
+spect_status spect_em_step_reg(spect_plan plan, float* x, const float* y, const float* rbar, const float* u,
+                               float beta, int niter, spect_stream stream);
+
+/*
  * spect_sensitivity -- copy the plan's sensitivity s = A'1 (the d(0) term
  * of Eq. (8)) into s (device, nx*ny*nz).  Computes and caches it first if
  * needed.  Errors as spect_forward.

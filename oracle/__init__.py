@@ -223,6 +223,46 @@ def em_step(x, y, rbar, mu, psf, dy: float, angles, s=None, nthreads: int = 0) -
     return out
 
 
+def em_step_reg(x, y, rbar, u, beta: float, mu, psf, dy: float, angles, s=None, nthreads: int = 0) -> np.ndarray:
+    """One inner iteration of the regularised EM update, Eqs. (7)-(8):
+
+        x+ = (-d + sqrt(d^2 + 4 beta x e)) / (2 beta),
+        d = A'1 - beta u,   e = A'(y / (A x + rbar)),
+
+    the non-negative root of beta x^2 + d x - x_k e = 0 (the EM surrogate of
+    Eq. (6) with the penalty (beta/2)||x - u||^2).  Where d >= 0 it is written
+    as 2 x e / (d + sqrt(d^2 + 4 beta x e)) (no cancellation for small beta;
+    equals the MLEM update x e / A'1 at beta = 0), where d < 0 as Eq. (7)
+    itself (no cancellation there).
+    Guards as em_step: ratio 0 where A x + rbar <= 0; voxel 0 where the
+    result is not finite and positive.
+    """
+    x = _f64(x)
+    y = _f64(y)
+    u = _f64(u)
+    if s is None:
+        s = sensitivity(mu, psf, dy, angles, nthreads)
+    ybar = forward(x, mu, psf, dy, angles, nthreads)
+    if rbar is not None:
+        ybar = ybar + _f64(rbar)
+    ratio = np.zeros_like(ybar)
+    pos = ybar > 0
+    ratio[pos] = y[pos] / ybar[pos]
+    e = back(ratio, mu, psf, dy, angles, nthreads)
+    d = s - beta * u
+    xe = x * e
+    root = np.sqrt(d * d + 4.0 * beta * xe)
+    out = np.zeros_like(x)
+    pos = d >= 0
+    den = d + root
+    ok = pos & (den > 0)
+    out[ok] = 2.0 * xe[ok] / den[ok]
+    neg = ~pos
+    if beta > 0:
+        out[neg] = (root[neg] - d[neg]) / (2.0 * beta)
+    return out
+
+
 def poisson_loglik(x, y, rbar, mu, psf, dy: float, angles, nthreads: int = 0) -> float:
     """-f(x) of Eq. (4) (up to the constant log y!): y' log(Ax + r) - 1'(Ax + r)."""
     ybar = forward(x, mu, psf, dy, angles, nthreads)

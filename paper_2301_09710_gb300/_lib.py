@@ -64,6 +64,8 @@ def load(path: str = LIB_PATH):
         lib.spect_back.restype = st
         lib.spect_em_step.argtypes = [vp, vp, vp, vp, i, vp]
         lib.spect_em_step.restype = st
+        lib.spect_em_step_reg.argtypes = [vp, vp, vp, vp, vp, ctypes.c_float, i, vp]
+        lib.spect_em_step_reg.restype = st
         lib.spect_sensitivity.argtypes = [vp, vp, vp]
         lib.spect_sensitivity.restype = st
         lib.spect_plan_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),

@@ -1,0 +1,141 @@
+"""Differentiation through the projector (Section II-A, "customized the chain rule")
+and the unrolled CNN-regularised EM of Algorithm 3 (Section II-B).
+
+* ``project(x, plan)`` is A x with backward A' g; ``backproject(v, plan)`` is A' v
+  with backward A g.  Both run the library's kernels (the transpose is exact, so
+  these are the true Jacobians) and never store rotated intermediates.
+* ``em_update`` is one inner iteration of Eqs. (7)-(8) written with them, so
+  gradients flow through A, A' and the closed-form update.
+* ``UnrolledEM`` unrolls K outer iterations u = g_theta(x_k), x_{k+1} = EM(x_k, u)
+  with a small 3D CNN g_theta and per-iteration activation checkpointing
+  (``torch.utils.checkpoint``): only the iterates are kept, everything inside an
+  iteration is recomputed in the backward pass.
+
+The CNN uses torch's conv3d (it is not part of the projector path).
+"""
+from __future__ import annotations
+
+import torch
+import torch.nn as nn
+import torch.utils.checkpoint as ckpt
+
+from .projector import SpectPlan
+
+
+class _Project(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, plan):
+        ctx.plan = plan
+        return plan.forward(x.contiguous())
+
+    @staticmethod
+    def backward(ctx, g):
+        return ctx.plan.back(g.contiguous()), None
+
+
+class _BackProject(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, v, plan):
+        ctx.plan = plan
+        return plan.back(v.contiguous())
+
+    @staticmethod
+    def backward(ctx, g):
+        return ctx.plan.forward(g.contiguous()), None
+
+
+def project(x: torch.Tensor, plan) -> torch.Tensor:
+    """v = A x, differentiable (backward: A')."""
+    return _Project.apply(x, plan)
+
+
+def backproject(v: torch.Tensor, plan) -> torch.Tensor:
+    """x = A' v, differentiable (backward: A)."""
+    return _BackProject.apply(v, plan)
+
+
+def em_update(x, y, rbar, plan, s, u=None, beta: float = 0.0):
+    """One inner EM iteration, Eqs. (7)-(8), differentiable in x and u.
+
+    beta == 0: x e / s (MLEM).  beta > 0: the non-negative root of
+    beta x'^2 + d x' - x e = 0, d = s - beta u, in the cancellation-free form
+    for the sign of d.  Guards as the library: ratio 0 where A x + rbar <= 0.
+    """
+    ybar = project(x, plan)
+    if rbar is not None:
+        ybar = ybar + rbar
+    pos = ybar > 0
+    ratio = torch.where(pos, y / torch.where(pos, ybar, torch.ones_like(ybar)), torch.zeros_like(ybar))
+    e = backproject(ratio, plan)
+    xe = x * e
+    if beta == 0.0 or u is None:
+        ok = s > 0
+        return torch.where(ok, xe / torch.where(ok, s, torch.ones_like(s)), torch.zeros_like(x))
+    d = s - beta * u
+    root = torch.sqrt(d * d + 4.0 * beta * xe)
+    dpos = d >= 0
+    den = d + root
+    safe = dpos & (den > 0)
+    a = 2.0 * xe / torch.where(safe, den, torch.ones_like(den))
+    b = (root - d) / (2.0 * beta)
+    return torch.where(safe, a, torch.where(dpos, torch.zeros_like(a), b))
+
+
+class Regularizer3D(nn.Module):
+    """g_theta: 3 conv3d layers (3x3x3), ReLU between them, residual on the input
+    (Section III-B: a 3-layer CNN with ReLU except after the last layer)."""
+
+    def __init__(self, channels: int = 8):
+        super().__init__()
+        self.c1 = nn.Conv3d(1, channels, 3, padding=1)
+        self.c2 = nn.Conv3d(channels, channels, 3, padding=1)
+        self.c3 = nn.Conv3d(channels, 1, 3, padding=1)
+        for m in (self.c1, self.c2, self.c3):
+            nn.init.normal_(m.weight, std=0.02)
+            nn.init.zeros_(m.bias)
+
+    def forward(self, x):  # x: (nz, ny, nx)
+        h = x[None, None]
+        h = torch.relu(self.c1(h))
+        h = torch.relu(self.c2(h))
+        return x + self.c3(h)[0, 0]
+
+
+class UnrolledEM(nn.Module):
+    """Algorithm 3 unrolled: K outer iterations of u = g(x_k) and n_inner EM updates.
+
+    ``checkpoint=True`` recomputes each outer iteration in the backward pass, so
+    memory holds only the K+1 iterates (the paper's motivation for end-to-end
+    training without storing rotated intermediates, Section IV).
+    """
+
+    def __init__(self, plan: SpectPlan, n_outer: int = 3, n_inner: int = 1, beta: float = 1.0,
+                 channels: int = 8, checkpoint: bool = True, cnn: nn.Module | None = None):
+        super().__init__()
+        self.plan = plan
+        self.n_outer, self.n_inner, self.beta = int(n_outer), int(n_inner), float(beta)
+        self.cnn = cnn if cnn is not None else Regularizer3D(channels)
+        self.checkpoint = checkpoint
+        self._s = None
+
+    def sensitivity(self):
+        if self._s is None:
+            with torch.no_grad():
+                self._s = self.plan.sensitivity()
+        return self._s
+
+    def outer(self, x, y, rbar):
+        s = self.sensitivity()
+        u = self.cnn(x)
+        for _ in range(self.n_inner):
+            x = em_update(x, y, rbar, self.plan, s, u, self.beta)
+        return x
+
+    def forward(self, x0, y, rbar=None):
+        x = x0
+        for _ in range(self.n_outer):
+            if self.checkpoint and torch.is_grad_enabled():
+                x = ckpt.checkpoint(self.outer, x, y, rbar, use_reentrant=False)
+            else:
+                x = self.outer(x, y, rbar)
+        return x

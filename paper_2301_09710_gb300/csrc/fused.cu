@@ -719,7 +719,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
 }
 
 // x_t(q,k) (+)= sum_{v in chunk} sum_{e < MAXE} w_e t[v][p_e][k]
-// with the MLEM update x <- x e / s on the last chunk when em_x is set.  The
+// with the EM update (em_update) on the last chunk when em.x is set.  The
 // lists are laid out [q][l][e] so one destination's entries for all views are
 // contiguous; each entry holds the premultiplied offset p*nz of its source
 // column in the slab.  A thread owns VEC consecutive k of one destination (float4 loads
@@ -739,7 +739,7 @@ struct VecT<4> {
 template <int MAXE, int VEC>
 __global__ void __launch_bounds__(256) k_adj_rot_t(Geometry g, int ps, const AdjEntry* __restrict__ adj,
                                                    const float* __restrict__ slab, int l0, int nv, float* out,
-                                                   int accumulate, float* em_x, const float* __restrict__ em_s)
+                                                   int accumulate, EmArgs em)
 {
     using VT = typename VecT<VEC>::type;
     const int nxy = g.nx * g.ny;
@@ -817,12 +817,8 @@ __global__ void __launch_bounds__(256) k_adj_rot_t(Geometry g, int ps, const Adj
     for (int u = 0; u < VEC; ++u) {
         float val = acc[u].value();
         if (accumulate) val += out[o + u];
-        if (em_x) {
-            const float sv = em_s[o + u];
-            em_x[o + u] = sv > 0.f ? (em_x[o + u] * val) / sv : 0.f;
-        } else {
-            out[o + u] = val;
-        }
+        if (em.x) em.x[o + u] = em_update(em.x[o + u], val, em.s[o + u], em.u ? em.u[o + u] : 0.f, em.beta);
+        else out[o + u] = val;
     }
 }
 
@@ -985,8 +981,8 @@ cudaError_t launch_fwd_reduce(const spect_plan_s& P, float* v, const float* em_y
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_rot_t(const spect_plan_s& P, int l0, int nv, float* out, int accumulate, float* em_x,
-                             const float* em_s, cudaStream_t st)
+cudaError_t launch_adj_rot_t(const spect_plan_s& P, int l0, int nv, float* out, int accumulate, EmArgs em,
+                             cudaStream_t st)
 {
     const bool vec4 = (P.g.nz % 4) == 0;
     const size_t n = (size_t)P.g.nx * P.g.ny * (vec4 ? P.g.nz / 4 : P.g.nz);
@@ -995,9 +991,9 @@ cudaError_t launch_adj_rot_t(const spect_plan_s& P, int l0, int nv, float* out, 
 #define SPECT_ADJ(M)                                                                                                 \
     case M:                                                                                                          \
         if (vec4)                                                                                                    \
-            k_adj_rot_t<M, 4><<<blocks, 256, 0, st>>>(P.g, P.ps, P.adjf, P.slab, l0, nv, out, accumulate, em_x, em_s); \
+            k_adj_rot_t<M, 4><<<blocks, 256, 0, st>>>(P.g, P.ps, P.adjf, P.slab, l0, nv, out, accumulate, em); \
         else                                                                                                         \
-            k_adj_rot_t<M, 1><<<blocks, 256, 0, st>>>(P.g, P.ps, P.adjf, P.slab, l0, nv, out, accumulate, em_x, em_s); \
+            k_adj_rot_t<M, 1><<<blocks, 256, 0, st>>>(P.g, P.ps, P.adjf, P.slab, l0, nv, out, accumulate, em); \
         break;
         SPECT_ADJ(1) SPECT_ADJ(2) SPECT_ADJ(3) SPECT_ADJ(4) SPECT_ADJ(5) SPECT_ADJ(6) SPECT_ADJ(7) SPECT_ADJ(8)
 #undef SPECT_ADJ

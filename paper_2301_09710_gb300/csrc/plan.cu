@@ -109,7 +109,7 @@ void free_plan(spect_plan_s* P)
     }
     for (cudaEvent_t e : P->evpool) cudaEventDestroy(e);
     void* ptrs[] = {P->mu, P->psf, P->psf_adj, P->fx, P->fz, P->fx_adj, P->fz_adj, P->rot, P->adj_off, P->adj,
-                    P->slab, P->e, P->ratio, P->s, P->mubar, P->xt, P->et, P->st, P->part, P->adjf, P->err, P->rtab};
+                    P->slab, P->e, P->ratio, P->s, P->mubar, P->xt, P->et, P->st, P->part, P->adjf, P->err, P->rtab, P->ut};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete P;
@@ -184,8 +184,8 @@ spect_status run_forward(spect_plan_s* P, const float* x, float* v, const float*
     return SPECT_OK;
 }
 
-// out = A' v; with em_x set, the last chunk writes x <- x * out / s into em_x instead.
-spect_status run_back(spect_plan_s* P, const float* v, float* out, float* em_x, const float* em_s, cudaStream_t st)
+// out = A' v; with em.x set, the last chunk applies the EM update to em.x instead.
+spect_status run_back(spect_plan_s* P, const float* v, float* out, spect::EmArgs em, cudaStream_t st)
 {
     const int nview = P->g.nview;
     for (int l0 = 0; l0 < nview; l0 += P->chunk) {
@@ -193,9 +193,10 @@ spect_status run_back(spect_plan_s* P, const float* v, float* out, float* em_x, 
         const bool last = l0 + nv >= nview;
         SPECT_CUDA_TRY(counted(P, SPECT_K_CONV_ADJ, st, [&] { return spect::launch_conv_adjoint(*P, v, l0, nv, st); }),
                        "PSF blur adjoint launch");
-        float* emx = (last && em_x) ? em_x : nullptr;
+        spect::EmArgs e = em;
+        if (!last) e.x = nullptr;
         SPECT_CUDA_TRY(counted(P, SPECT_K_ROTATE_ADJ, st,
-                               [&] { return spect::launch_rotate_adjoint(*P, l0, nv, out, l0 > 0, emx, em_s, emx, st); }),
+                               [&] { return spect::launch_rotate_adjoint(*P, l0, nv, out, l0 > 0, e, st); }),
                        "adjoint rotation launch");
     }
     return SPECT_OK;
@@ -237,9 +238,8 @@ spect_status fast_forward(spect_plan_s* P, const float* xt, float* v, const floa
     return SPECT_OK;
 }
 
-// out_t = A' v (internal layout); with em_xt set the last chunk applies x <- x out / s_t instead
-spect_status fast_back(spect_plan_s* P, const float* v, float* out_t, float* em_xt, const float* em_st,
-                       cudaStream_t st)
+// out_t = A' v (internal layout); with em.x set the last chunk applies the EM update instead
+spect_status fast_back(spect_plan_s* P, const float* v, float* out_t, spect::EmArgs em, cudaStream_t st)
 {
     const int nview = P->g.nview;
     for (int l0 = 0; l0 < nview; l0 += P->adj_chunk) {
@@ -247,9 +247,10 @@ spect_status fast_back(spect_plan_s* P, const float* v, float* out_t, float* em_
         const bool last = l0 + nv >= nview;
         SPECT_CUDA_TRY(counted(P, SPECT_K_CONV_ADJ, st, [&] { return spect::launch_fused_adjoint(*P, v, l0, nv, st); }),
                        "fused adjoint launch");
-        float* emx = (last && em_xt) ? em_xt : nullptr;
+        spect::EmArgs e = em;
+        if (!last) e.x = nullptr;
         SPECT_CUDA_TRY(counted(P, SPECT_K_ROTATE_ADJ, st,
-                               [&] { return spect::launch_adj_rot_t(*P, l0, nv, out_t, l0 > 0, emx, em_st, st); }),
+                               [&] { return spect::launch_adj_rot_t(*P, l0, nv, out_t, l0 > 0, e, st); }),
                        "adjoint rotation launch");
     }
     return SPECT_OK;
@@ -261,8 +262,8 @@ spect_status ensure_sensitivity(spect_plan_s* P, cudaStream_t st)
     const size_t nproj = (size_t)P->g.nx * P->g.nz * P->g.nview;
     SPECT_CUDA_TRY(counted(P, SPECT_K_OTHER, st, [&] { return spect::launch_fill(P->ratio, nproj, 1.f, st); }),
                    "fill launch");
-    spect_status r = P->fast ? fast_back(P, P->ratio, P->st, nullptr, nullptr, st)
-                             : run_back(P, P->ratio, P->s, nullptr, nullptr, st);
+    spect_status r = P->fast ? fast_back(P, P->ratio, P->st, spect::EmArgs(), st)
+                             : run_back(P, P->ratio, P->s, spect::EmArgs(), st);
     if (r != SPECT_OK) return r;
     if (P->fast) {
         r = from_internal(P, P->st, P->s, st);
@@ -490,6 +491,7 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
         PLAN_ALLOC(P->xt, vol, "internal image");
         PLAN_ALLOC(P->et, vol, "internal back-projection");
         PLAN_ALLOC(P->st, vol, "internal sensitivity");
+        PLAN_ALLOC(P->ut, vol, "internal regulariser target");
         PLAN_ALLOC(P->part, nproj * (size_t)spect::fused_groups(*P), "depth-group partial sums");
         // mu in the [j][i][k] layout (temporary, the slab serves as scratch)
         PLAN_TRY(spect::launch_transpose(P->mu, P->slab, nz, (int)nxy, st), "mu transpose launch");
@@ -532,11 +534,11 @@ spect_status spect_back(spect_plan P, const float* v, float* x, spect_stream str
     if (r != SPECT_OK) return r;
     cudaStream_t st = (cudaStream_t)stream;
     if (P->fast) {
-        r = fast_back(P, v, P->et, nullptr, nullptr, st);
+        r = fast_back(P, v, P->et, spect::EmArgs(), st);
         if (r != SPECT_OK) return r;
         return from_internal(P, P->et, x, st);
     }
-    return run_back(P, v, x, nullptr, nullptr, st);
+    return run_back(P, v, x, spect::EmArgs(), st);
 }
 
 spect_status spect_sensitivity(spect_plan P, float* s, spect_stream stream)
@@ -553,29 +555,50 @@ spect_status spect_sensitivity(spect_plan P, float* s, spect_stream stream)
 
 spect_status spect_em_step(spect_plan P, float* x, const float* y, const float* rbar, int niter, spect_stream stream)
 {
+    return spect_em_step_reg(P, x, y, rbar, nullptr, 0.f, niter, stream);
+}
+
+spect_status spect_em_step_reg(spect_plan P, float* x, const float* y, const float* rbar, const float* u, float beta,
+                               int niter, spect_stream stream)
+{
     spect_status r = check_call(P, x, y, "x", "y");
     if (r != SPECT_OK) return r;
     if (rbar && !aligned16(rbar)) return fail(SPECT_EINVAL, "rbar is not 16-byte aligned");
     if (niter < 0) return fail(SPECT_EINVAL, "niter must be >= 0");
+    if (!(beta >= 0.f) || !isfinite(beta)) return fail(SPECT_EINVAL, "beta must be finite and >= 0");
+    if (beta > 0.f && !u) return fail(SPECT_EINVAL, "u is required when beta > 0");
+    if (u && !aligned16(u)) return fail(SPECT_EINVAL, "u is not 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     r = ensure_sensitivity(P, st);
     if (r != SPECT_OK) return r;
+    if (niter == 0) return SPECT_OK;
+    spect::EmArgs em;
+    em.beta = beta > 0.f ? beta : 0.f;
     if (P->fast) {
-        if (niter == 0) return SPECT_OK;
         r = to_internal(P, x, P->xt, st);
         if (r != SPECT_OK) return r;
+        if (em.beta > 0.f) {
+            r = to_internal(P, u, P->ut, st);
+            if (r != SPECT_OK) return r;
+            em.u = P->ut;
+        }
+        em.x = P->xt;
+        em.s = P->st;
         for (int it = 0; it < niter; ++it) {
             r = fast_forward(P, P->xt, P->ratio, y, rbar, st);
             if (r != SPECT_OK) return r;
-            r = fast_back(P, P->ratio, P->et, P->xt, P->st, st);
+            r = fast_back(P, P->ratio, P->et, em, st);
             if (r != SPECT_OK) return r;
         }
         return from_internal(P, P->xt, x, st);
     }
+    em.x = x;
+    em.s = P->s;
+    em.u = em.beta > 0.f ? u : nullptr;
     for (int it = 0; it < niter; ++it) {
         r = run_forward(P, x, P->ratio, y, rbar, st);
         if (r != SPECT_OK) return r;
-        r = run_back(P, P->ratio, P->e, x, P->s, st);
+        r = run_back(P, P->ratio, P->e, em, st);
         if (r != SPECT_OK) return r;
     }
     return SPECT_OK;

@@ -48,14 +48,14 @@ cudaError_t launch_rotate_atten(const spect_plan_s& P, const float* x, int l0, i
 // K1T: out(q,k) (+)= sum_{v in chunk} sum_{(p,w) in adj(l0+v, q)} w * t(p,k; v)
 // The adjacency list of destination q holds every rotated-frame pixel p whose
 // bilinear stencil covers q, with the same FP32 weight K1 uses.
-// With em_xout set, the final value e is turned into the MLEM update
-// x <- x e / s (x = em_x, s = em_s) instead of being stored.
+// With em.x set, the final value e is turned into the EM update of em.x
+// (em_update: MLEM, or the regularised form when em.beta > 0) instead of
+// being stored.
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_rotate_adjoint(Geometry g, const int* __restrict__ adj_off,
                                                         const AdjEntry* __restrict__ adj,
                                                         const float* __restrict__ slab, int l0, int nv,
-                                                        float* out, int accumulate, const float* em_x,
-                                                        const float* __restrict__ em_s, float* em_xout)
+                                                        float* out, int accumulate, EmArgs em)
 {
     const size_t nxy = (size_t)g.nx * g.ny;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -74,21 +74,17 @@ __global__ void __launch_bounds__(256) k_rotate_adjoint(Geometry g, const int* _
     const size_t o = k * nxy + q;
     float val = acc.value();
     if (accumulate) val += out[o];
-    if (em_xout) {
-        const float s = em_s[o];
-        em_xout[o] = s > 0.f ? (em_x[o] * val) / s : 0.f;
-    } else {
-        out[o] = val;
-    }
+    if (em.x) em.x[o] = em_update(em.x[o], val, em.s[o], em.u ? em.u[o] : 0.f, em.beta);
+    else out[o] = val;
 }
 
-cudaError_t launch_rotate_adjoint(const spect_plan_s& P, int l0, int nv, float* out, int accumulate,
-                                  const float* em_x, const float* em_s, float* em_xout, cudaStream_t st)
+cudaError_t launch_rotate_adjoint(const spect_plan_s& P, int l0, int nv, float* out, int accumulate, EmArgs em,
+                                  cudaStream_t st)
 {
     const Geometry& g = P.g;
     const size_t n = (size_t)g.nx * g.ny * g.nz;
     k_rotate_adjoint<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, P.adj_off, P.adj, P.slab, l0, nv, out,
-                                                                  accumulate, em_x, em_s, em_xout);
+                                                                  accumulate, em);
     return cudaGetLastError();
 }
 

@@ -83,6 +83,7 @@ struct spect_plan_s {
     float* xt = nullptr;         // nx*ny*nz, [j][i][k] image
     float* et = nullptr;         // nx*ny*nz, [j][i][k] back-projection accumulator
     float* st = nullptr;         // nx*ny*nz, [j][i][k] sensitivity
+    float* ut = nullptr;         // nx*ny*nz, [j][i][k] regulariser target of the regularised EM
     float* part = nullptr;       // G * nx*nz*nview forward partial sums
     spect::AdjEntry* adjf = nullptr;  // nview*nx*ny*adj_max fixed-length lists
     int ps = 0;                  // plane stride of the attenuation cache and slab: nx*nz rounded up to 4
@@ -177,6 +178,32 @@ struct AttenScan {
     }
 };
 
+// EM update of one voxel from its back-projected ratio e (Eqs. (7)-(8)):
+// MLEM x e / s when beta == 0; otherwise the non-negative root of
+// beta x'^2 + (s - beta u) x' - x e = 0, evaluated in the cancellation-free
+// form for the sign of d = s - beta u.  Non-positive denominators give 0.
+__device__ __forceinline__ float em_update(float x, float e, float s, float u, float beta)
+{
+    const float xe = x * e;
+    if (beta == 0.f) return s > 0.f ? xe / s : 0.f;
+    const float d = s - beta * u;
+    const float root = sqrtf(fmaf(d, d, 4.f * beta * xe));
+    if (d >= 0.f) {
+        const float den = d + root;
+        return den > 0.f ? (2.f * xe) / den : 0.f;
+    }
+    return (root - d) / (2.f * beta);
+}
+
+// Arguments of the EM epilogue of the adjoint-rotation kernels; x == nullptr
+// means plain back-projection.
+struct EmArgs {
+    float* x = nullptr;        // updated in place
+    const float* s = nullptr;  // sensitivity A'1 (same layout as x)
+    const float* u = nullptr;  // regulariser target (beta > 0 only)
+    float beta = 0.f;
+};
+
 // Kahan-compensated accumulator for depth and view sums.
 struct KSum {
     float s = 0.f, c = 0.f;
@@ -266,8 +293,8 @@ spect_status set_error(spect_status st, const char* msg);
 // All return the cudaError_t of the launch (cudaGetLastError()).
 cudaError_t launch_build_adjacency(const spect_plan_s& P, int pass, int* counts, int* maxcount, cudaStream_t st);
 cudaError_t launch_rotate_atten(const spect_plan_s& P, const float* x, int l0, int nv, cudaStream_t st);
-cudaError_t launch_rotate_adjoint(const spect_plan_s& P, int l0, int nv, float* out, int accumulate,
-                                  const float* em_x, const float* em_s, float* em_xout, cudaStream_t st);
+cudaError_t launch_rotate_adjoint(const spect_plan_s& P, int l0, int nv, float* out, int accumulate, EmArgs em,
+                                  cudaStream_t st);
 cudaError_t launch_conv_forward(const spect_plan_s& P, float* v, int l0, int nv, const float* em_y,
                                 const float* em_rbar, cudaStream_t st);
 cudaError_t launch_conv_adjoint(const spect_plan_s& P, const float* v, int l0, int nv, cudaStream_t st);
@@ -286,8 +313,8 @@ size_t fused_slab_per_view(const spect_plan_s& P);
 cudaError_t launch_fused_adjoint(const spect_plan_s& P, const float* v, int l0, int nv, cudaStream_t st);
 cudaError_t launch_fwd_reduce(const spect_plan_s& P, float* v, const float* em_y, const float* em_rbar,
                               cudaStream_t st);
-cudaError_t launch_adj_rot_t(const spect_plan_s& P, int l0, int nv, float* out, int accumulate, float* em_x,
-                             const float* em_s, cudaStream_t st);
+cudaError_t launch_adj_rot_t(const spect_plan_s& P, int l0, int nv, float* out, int accumulate, EmArgs em,
+                             cudaStream_t st);
 bool direct_fits(const Geometry& g, size_t smem_limit);
 cudaError_t launch_fill(float* p, size_t n, float value, cudaStream_t st);
 

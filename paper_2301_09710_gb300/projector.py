@@ -147,6 +147,18 @@ class SpectPlan:
                                           _stream_handle(stream)))
         return x
 
+    def em_step_reg(self, x, y, u, beta: float, rbar=None, niter: int = 1, stream=None) -> torch.Tensor:
+        """niter in-place regularised EM updates (Eqs. (7)-(8)) towards u with weight beta."""
+        self._check(x, self.vol_shape, "x")
+        self._check(y, self.proj_shape, "y")
+        if u is not None:
+            self._check(u, self.vol_shape, "u")
+        if rbar is not None:
+            self._check(rbar, self.proj_shape, "rbar")
+        _lib.check(self.lib.spect_em_step_reg(self.handle, _ptr(x), _ptr(y), _ptr(rbar), _ptr(u),
+                                              ctypes.c_float(beta), int(niter), _stream_handle(stream)))
+        return x
+
     def sensitivity(self, stream=None) -> torch.Tensor:
         """s = A' 1."""
         s = torch.empty(self.vol_shape, device=self.device, dtype=torch.float32)

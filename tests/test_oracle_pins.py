@@ -340,3 +340,39 @@ def test_em_loglik_monotone_and_positive():
         assert np.all(x[s > 0] > 0)
         ll.append(oracle.poisson_loglik(x, y, rbar, prob.mu, psf, prob.dy, ang))
     assert all(b >= a - 1e-9 * abs(a) for a, b in zip(ll, ll[1:])), ll
+
+
+# ------------------------------------------------------------------ regularised EM (Eqs. (7)-(8))
+def test_em_reg_reduces_to_mlem_as_beta_vanishes():
+    prob, psf, ang = _em_problem()
+    rng = np.random.default_rng(17)
+    y = rng.poisson(5.0, (prob.nview, 6, 16)).astype(np.float64)
+    x = np.ones((6, 16, 16))
+    u = rng.uniform(0, 2, x.shape)
+    mlem = oracle.em_step(x, y, None, prob.mu, psf, prob.dy, ang)
+    reg = oracle.em_step_reg(x, y, None, u, 1e-12, prob.mu, psf, prob.dy, ang)
+    np.testing.assert_allclose(reg, mlem, rtol=1e-9)
+
+
+def test_em_reg_solves_the_surrogate_quadratic():
+    # the update is the non-negative root of beta x^2 + d x - x_k e = 0 with
+    # d = A'1 - beta u and e = A'(y / (A x_k + rbar)) (the EM surrogate)
+    prob, psf, ang = _em_problem()
+    rng = np.random.default_rng(18)
+    xk = rng.uniform(0.5, 2, (6, 16, 16))
+    y = rng.poisson(8.0, (prob.nview, 6, 16)).astype(np.float64)
+    rbar = np.full_like(y, 0.3)
+    u = rng.uniform(0.5, 3, xk.shape)
+    beta = 0.7
+    s = oracle.sensitivity(prob.mu, psf, prob.dy, ang)
+    xn = oracle.em_step_reg(xk, y, rbar, u, beta, prob.mu, psf, prob.dy, ang, s=s)
+    ybar = oracle.forward(xk, prob.mu, psf, prob.dy, ang) + rbar
+    e = oracle.back(y / ybar, prob.mu, psf, prob.dy, ang)
+    d = s - beta * u
+    resid = beta * xn ** 2 + d * xn - xk * e
+    scale = np.abs(xk * e).max()
+    assert np.abs(resid).max() <= 1e-12 * scale
+    assert np.all(xn >= 0)
+    # and large beta pulls the update towards u
+    xb = oracle.em_step_reg(xk, y, rbar, u, 1e9, prob.mu, psf, prob.dy, ang, s=s)
+    np.testing.assert_allclose(xb, u, rtol=1e-5)
