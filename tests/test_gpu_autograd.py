@@ -93,20 +93,27 @@ def test_unrolled_em_gradient_finite_differences():
     loss.backward()
     params = list(net.cnn.parameters())
     rng = np.random.default_rng(7)
-    dirs = [torch.from_numpy(rng.normal(0, 1, p.shape).astype(np.float32)).cuda() for p in params]
+    # a probe direction on the scale of the weights, small enough that ReLU
+    # patterns and the update's branches do not change
+    dirs = [torch.from_numpy(rng.normal(0, 0.05, p.shape).astype(np.float32)).cuda() for p in params]
     g_dot = sum((p.grad * d).sum().item() for p, d in zip(params, dirs))
-    eps = 1e-2
-    with torch.no_grad():
-        for p, d in zip(params, dirs):
-            p.add_(eps * d)
-        lp = loss_fn().item()
-        for p, d in zip(params, dirs):
-            p.add_(-2 * eps * d)
-        lm = loss_fn().item()
-        for p, d in zip(params, dirs):
-            p.add_(eps * d)
-    fd = (lp - lm) / (2 * eps)
-    assert abs(fd - g_dot) <= 2e-2 * abs(g_dot) + 1e-6, (fd, g_dot)
+
+    def central(eps):
+        with torch.no_grad():
+            for p, d in zip(params, dirs):
+                p.add_(eps * d)
+            lp = loss_fn().item()
+            for p, d in zip(params, dirs):
+                p.add_(-2 * eps * d)
+            lm = loss_fn().item()
+            for p, d in zip(params, dirs):
+                p.add_(eps * d)
+        return (lp - lm) / (2 * eps)
+
+    # Richardson-extrapolated central difference; the loss is evaluated in FP32,
+    # so this is a coarse check (the tight one is the FP64 oracle network below)
+    fd = (4 * central(1e-2) - central(2e-2)) / 3
+    assert abs(fd - g_dot) <= 5e-2 * abs(g_dot) + 1e-6, (fd, g_dot)
 
 
 class _OracleProject(torch.autograd.Function):
