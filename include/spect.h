@@ -186,6 +186,20 @@ spect_status spect_sensitivity(spect_plan plan, float* s, spect_stream stream);
 spect_status spect_plan_info(spect_plan plan, int* separable, int* fused, int* view_chunk, size_t* device_bytes);
 
 /*
+ * spect_plan_bytes -- an upper bound of the device memory (bytes, host
+ * out-pointer) that spect_plan_create would allocate for this geometry on the
+ * current device, without allocating anything: for admission control by a
+ * server that holds many plans (the paper has no counterpart).  Arguments as
+ * spect_plan_create; separable = 1 when the plan will use the separable
+ * factors (psf_fx/psf_fz given, and either no full psf or
+ * SPECT_PLAN_PREFER_SEPARABLE).  spect_plan_info reports the exact figure of a
+ * created plan, which never exceeds this bound.
+ * Errors: SPECT_EINVAL (arguments as spect_plan_create), SPECT_ECUDA.
+ */
+spect_status spect_plan_bytes(int nx, int ny, int nz, int nview, int px, int pz, int nview_psf, int separable,
+                              unsigned flags, size_t* bytes);
+
+/*
  * spect_fp32_peak -- measure the FP32 fused multiply-add throughput of the
  * current device with a register-resident dependent-chain kernel (no memory
  * traffic): tflops_ffma for scalar fmaf, tflops_ffma2 for the packed
@@ -231,9 +245,29 @@ spect_status spect_profile_read(spect_plan plan, long long* launches, double* ms
  */
 spect_status spect_plan_check(spect_plan plan);
 
+/*
+ * spect_plan_check_stream -- as spect_plan_check, but synchronises only
+ * `stream` (the caller has put all of the plan's work on it), so work of
+ * other plans on other streams keeps running.  For servers that interleave
+ * many plans (the paper has no counterpart).
+ */
+spect_status spect_plan_check_stream(spect_plan plan, spect_stream stream);
+
 /* spect_plan_destroy -- release the plan; NULL is accepted and returns OK.
  * Waits for the plan's outstanding work on the device before freeing. */
 spect_status spect_plan_destroy(spect_plan plan);
+
+/*
+ * spect_plan_release -- release the plan in stream order: its device memory
+ * is returned after the work already enqueued on `stream`, and the call does
+ * not wait for the device.  The caller guarantees that no work of the plan
+ * is pending on any other stream.  The handle is invalid afterwards; NULL is
+ * accepted.  Plan memory comes from the device's stream-ordered allocator
+ * (cudaMallocAsync on the creation stream) where the device supports it, so
+ * creating and releasing plans never synchronises the whole device (the paper
+ * has no counterpart).
+ */
+spect_status spect_plan_release(spect_plan plan, spect_stream stream);
 
 /*
  * spect_forward_static -- v = A x without any device allocation.

@@ -81,8 +81,14 @@ def load(path: str = LIB_PATH):
         lib.spect_forward_static.restype = st
         lib.spect_plan_check.argtypes = [vp]
         lib.spect_plan_check.restype = st
+        lib.spect_plan_bytes.argtypes = [i, i, i, i, i, i, i, i, ctypes.c_uint, ctypes.POINTER(ctypes.c_size_t)]
+        lib.spect_plan_bytes.restype = st
+        lib.spect_plan_check_stream.argtypes = [vp, vp]
+        lib.spect_plan_check_stream.restype = st
         lib.spect_plan_destroy.argtypes = [vp]
         lib.spect_plan_destroy.restype = st
+        lib.spect_plan_release.argtypes = [vp, vp]
+        lib.spect_plan_release.restype = st
         lib.spect_last_error.argtypes = []
         lib.spect_last_error.restype = ctypes.c_char_p
         lib.spect_version.argtypes = []

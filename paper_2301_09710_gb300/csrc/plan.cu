@@ -83,24 +83,45 @@ void spect::make_view_rot(int nx, int nview, const double* angles, ViewRot* out)
 
 namespace {
 
+// Plan memory is stream-ordered (cudaMallocAsync on the creation stream) when
+// the device has memory pools, so plans can be created and released while
+// other plans' kernels run, without a device-wide synchronisation.
+cudaError_t raw_alloc(spect_plan_s* P, void** p, size_t bytes, cudaStream_t st)
+{
+    return P->pooled ? cudaMallocAsync(p, bytes, st) : cudaMalloc(p, bytes);
+}
+
+void raw_free(spect_plan_s* P, void* p, cudaStream_t st)
+{
+    if (!p) return;
+    if (P->pooled) cudaFreeAsync(p, st);
+    else cudaFree(p);
+}
+
 template <class T>
 spect_status dalloc(spect_plan_s* P, T** p, size_t count, const char* what)
 {
     *p = nullptr;
     if (count == 0) return SPECT_OK;
     const size_t bytes = count * sizeof(T);
-    cudaError_t e = cudaMalloc((void**)p, bytes);
+    cudaError_t e = raw_alloc(P, (void**)p, bytes, P->home);
     if (e != cudaSuccess) {
         *p = nullptr;
         cudaGetLastError();
         return fail(e == cudaErrorMemoryAllocation ? SPECT_ENOMEM : SPECT_ECUDA,
                     std::string("allocating ") + what + ": " + cudaGetErrorString(e));
     }
+    // the kernels use 16-byte vector and bulk-copy accesses from these bases
+    if (((uintptr_t)*p & 255) != 0) {
+        raw_free(P, *p, P->home);
+        *p = nullptr;
+        return fail(SPECT_ECUDA, std::string("allocation of ") + what + " is not 256-byte aligned");
+    }
     P->bytes += bytes;
     return SPECT_OK;
 }
 
-void free_plan(spect_plan_s* P)
+void free_plan(spect_plan_s* P, cudaStream_t st)
 {
     if (!P) return;
     for (auto& p : P->pending) {
@@ -110,10 +131,12 @@ void free_plan(spect_plan_s* P)
     for (cudaEvent_t e : P->evpool) cudaEventDestroy(e);
     void* ptrs[] = {P->mu, P->psf, P->psf_adj, P->fx, P->fz, P->fx_adj, P->fz_adj, P->rot, P->adj_off, P->adj,
                     P->slab, P->e, P->ratio, P->s, P->mubar, P->xt, P->et, P->st, P->part, P->adjf, P->err, P->rtab, P->ut};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
+    for (void* p : ptrs) raw_free(P, p, st);
     delete P;
 }
+
+// a plan that failed during creation: its memory is freed on the creation stream
+void free_plan(spect_plan_s* P) { free_plan(P, P ? P->home : nullptr); }
 
 size_t slab_budget_bytes(bool fast)
 {
@@ -294,6 +317,74 @@ const char* spect_last_error(void) { return g_err.c_str(); }
 
 const char* spect_version(void) { return "spect-gb300 0.1 (sm_103a)"; }
 
+namespace {
+
+// Upper bound of the device bytes a plan of this geometry allocates (the sum
+// of the allocations in spect_plan_create, with the adjacency lists at their
+// largest: 8 fixed entries per list, or 4 entries per source pixel in the
+// compressed form, whichever is larger).  When the fused kernels serve a
+// geometry, their buffers dominate those of the low-memory path it may fall
+// back to, so the fused sizes bound both.
+size_t plan_bytes_bound(const spect_plan_s& P)
+{
+    const Geometry& g = P.g;
+    const size_t F = sizeof(float);
+    const size_t vol = (size_t)g.nx * g.ny * g.nz, nproj = (size_t)g.nx * g.nz * g.nview;
+    const size_t nxy = (size_t)g.nx * g.ny, nrows = (size_t)g.nvp * g.ny, nlist = nxy * g.nview;
+    size_t b = sizeof(int) + vol * F;
+    if (P.separable) b += ((size_t)g.px * 4 + (size_t)g.pz * (1 + P.cls_z)) * nrows * F;
+    else b += (size_t)g.px * g.pz * nrows * (1 + (size_t)P.cls_x * P.cls_z) * F;
+    b += (size_t)g.nview * sizeof(ViewRot);
+    const size_t fixed = nlist * 8 * sizeof(spect::AdjEntry);
+    const size_t csr = (nlist + 1) * sizeof(int) + 4 * nlist * sizeof(spect::AdjEntry);
+    b += P.fast ? std::max(fixed, csr) : csr;
+    const size_t per_view = std::max(vol, P.fast ? spect::fused_slab_per_view(P) : vol);
+    const size_t chunk = std::max<size_t>(1, std::min<size_t>((size_t)g.nview,
+                                                               slab_budget_bytes(P.fast) / (per_view * F)));
+    b += per_view * chunk * F;
+    b += (2 * vol + nproj) * F;
+    if (P.fast) {
+        b += (size_t)g.ny * P.ps * g.nview * F + 4 * vol * F;
+        b += nproj * (size_t)spect::fused_groups(P) * F + (size_t)g.nview * g.ny * P.ts * F;
+    }
+    return b;
+}
+
+}  // namespace
+
+spect_status spect_plan_bytes(int nx, int ny, int nz, int nview, int px, int pz, int nview_psf, int separable,
+                              unsigned flags, size_t* bytes)
+{
+    if (!bytes) return fail(SPECT_EINVAL, "bytes is NULL");
+    *bytes = 0;
+    if (nx != ny || nx < 2 || nx > 1024 || nz < 1 || nz > 4096 || nview < 1 || nview > 4096)
+        return fail(SPECT_EINVAL, "geometry out of range (as spect_plan_create)");
+    if (px < 1 || pz < 1 || px > 127 || pz > 127 || (px % 2) == 0 || (pz % 2) == 0)
+        return fail(SPECT_EINVAL, "PSF sizes px, pz must be odd and in [1, 127]");
+    if (nview_psf != 1 && nview_psf != nview) return fail(SPECT_EINVAL, "nview_psf must be 1 or nview");
+    int dev = 0, smem_optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SPECT_ECUDA, "device query failed");
+    }
+    spect_plan_s P;
+    Geometry& g = P.g;
+    g.nx = nx; g.ny = ny; g.nz = nz; g.nview = nview;
+    g.px = px; g.pz = pz; g.nvp = nview_psf;
+    P.separable = separable != 0;
+    P.ps = (nx * nz + 3) & ~3;
+    P.ts = (5 * nx + 3) & ~3;
+    P.cls_x = 3;
+    P.cls_z = nz >= 2 ? 3 : 1;
+    if (P.separable && !(flags & SPECT_PLAN_LOW_MEMORY)) {
+        P.bucket = spect::fused_bucket(g, (size_t)smem_optin);
+        P.fast = P.bucket > 0;
+    }
+    *bytes = plan_bytes_bound(P);
+    return SPECT_OK;
+}
+
 spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nview, const float* mu, float dy,
                                const float* psf, const float* psf_fx, const float* psf_fz, int px, int pz,
                                int nview_psf, const double* angles, unsigned flags, spect_stream stream)
@@ -323,6 +414,7 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
 
     cudaStream_t st = (cudaStream_t)stream;
     spect_plan_s* P = new spect_plan_s();
+    P->home = st;
     Geometry& g = P->g;
     g.nx = nx; g.ny = ny; g.nz = nz; g.nview = nview;
     g.px = px; g.pz = pz; g.nvp = nview_psf;
@@ -358,6 +450,11 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
 
     PLAN_TRY(cudaGetDevice(&dev), "cudaGetDevice");
     PLAN_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "device query");
+    {
+        int pools = 0;
+        PLAN_TRY(cudaDeviceGetAttribute(&pools, cudaDevAttrMemoryPoolsSupported, dev), "device query");
+        P->pooled = pools != 0;
+    }
     if (P->separable && !(flags & SPECT_PLAN_LOW_MEMORY)) {
         P->bucket = spect::fused_bucket(g, (size_t)smem_optin);
         P->fast = P->bucket > 0;
@@ -400,10 +497,10 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
         PLAN_ALLOC(P->psf_adj, n * P->cls_x * P->cls_z, "psf variants");
         PLAN_TRY(cudaMemcpyAsync(P->psf, psf, n * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy psf");
         float* scratch = nullptr;
-        PLAN_TRY(cudaMalloc((void**)&scratch, n * P->cls_x * sizeof(float)), "PSF variant scratch");
+        PLAN_TRY(raw_alloc(P, (void**)&scratch, n * P->cls_x * sizeof(float), st), "PSF variant scratch");
         cudaError_t e1 = spect::launch_psf_variants(*P, scratch, st);
+        raw_free(P, scratch, st);
         cudaError_t e2 = cudaStreamSynchronize(st);
-        cudaFree(scratch);
         PLAN_TRY(e1, "PSF variant launch");
         PLAN_TRY(e2, "PSF variant build");
     }
@@ -423,17 +520,17 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
         const size_t nlist = nxy * nview;
         int* d_counts = nullptr;
         int* d_max = nullptr;
-        PLAN_TRY(cudaMalloc((void**)&d_counts, nlist * sizeof(int)), "adjacency counts");
-        PLAN_TRY(cudaMalloc((void**)&d_max, sizeof(int)), "adjacency max");
+        PLAN_TRY(raw_alloc(P, (void**)&d_counts, nlist * sizeof(int), st), "adjacency counts");
+        PLAN_TRY(raw_alloc(P, (void**)&d_max, sizeof(int), st), "adjacency max");
         cudaMemsetAsync(d_max, 0, sizeof(int), st);
         cudaError_t e1 = spect::launch_build_adjacency(*P, 0, d_counts, d_max, st);
         std::vector<int> counts(nlist);
         int mx = 0;
         cudaError_t e2 = cudaMemcpyAsync(counts.data(), d_counts, nlist * sizeof(int), cudaMemcpyDeviceToHost, st);
         cudaError_t e3 = cudaMemcpyAsync(&mx, d_max, sizeof(int), cudaMemcpyDeviceToHost, st);
+        raw_free(P, d_counts, st);
+        raw_free(P, d_max, st);
         cudaError_t e4 = cudaStreamSynchronize(st);
-        cudaFree(d_counts);
-        cudaFree(d_max);
         PLAN_TRY(e1, "adjacency count launch");
         PLAN_TRY(e2, "adjacency counts download");
         PLAN_TRY(e3, "adjacency max download");
@@ -510,8 +607,21 @@ spect_status spect_plan_destroy(spect_plan P)
 {
     if (!P) return SPECT_OK;
     cudaError_t e = cudaDeviceSynchronize();
-    free_plan(P);
+    // the device is idle: free on the legacy default stream and wait, so the
+    // memory is back in the pool when this returns
+    free_plan(P, (cudaStream_t)0);
+    cudaError_t e2 = cudaStreamSynchronize((cudaStream_t)0);
+    if (e == cudaSuccess) e = e2;
     if (e != cudaSuccess) return fail(SPECT_ECUDA, std::string("synchronise before destroy: ") + cudaGetErrorString(e));
+    return SPECT_OK;
+}
+
+spect_status spect_plan_release(spect_plan P, spect_stream stream)
+{
+    if (!P) return SPECT_OK;
+    free_plan(P, (cudaStream_t)stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(SPECT_ECUDA, std::string("stream-ordered release: ") + cudaGetErrorString(e));
     return SPECT_OK;
 }
 
@@ -601,6 +711,20 @@ spect_status spect_em_step_reg(spect_plan P, float* x, const float* y, const flo
         r = run_back(P, P->ratio, P->e, em, st);
         if (r != SPECT_OK) return r;
     }
+    return SPECT_OK;
+}
+
+spect_status spect_plan_check_stream(spect_plan P, spect_stream stream)
+{
+    if (!P) return fail(SPECT_EINVAL, "plan is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, P->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && h != 0) e = cudaMemsetAsync(P->err, 0, sizeof(int), st);
+    if (e != cudaSuccess) return fail(SPECT_ECUDA, std::string("reading the plan's error word: ") + cudaGetErrorString(e));
+    if (h == SPECT_ETIMEOUT) return fail(SPECT_ETIMEOUT, "a bounded wait on a bulk copy ran out; outputs are invalid");
+    if (h != 0) return fail(SPECT_ECUDA, "device error word set");
     return SPECT_OK;
 }
 

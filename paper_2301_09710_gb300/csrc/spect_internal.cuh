@@ -74,6 +74,8 @@ struct spect_plan_s {
     int cls_x = 3, cls_z = 3;    // edge classes per axis for A' (1 when the axis has length 1)
     int sep_tk = 0;              // separable kernels: k-rows per block
     // fast path (fused kernels, k-fastest internal layout, cached attenuation)
+    cudaStream_t home = nullptr; // creation stream (stream-ordered allocations)
+    bool pooled = false;         // memory from cudaMallocAsync (freed with cudaFreeAsync)
     int fast = 0;                // 1 when the fused kernels serve this plan
     int bucket = 0;              // padded tap count of the fused kernels
     int fused_J = 8;             // depth planes per fused forward block

@@ -68,6 +68,17 @@ def forward_static(x, nview: int, fx, fz, mu=None, dy: float = 1.0, angles=None,
     return out
 
 
+def plan_bytes(nx: int, nz: int, nview: int, px: int, pz: int, nview_psf: int = 1, separable: bool = True,
+               low_memory: bool = False) -> int:
+    """Upper bound of the device bytes a plan of this geometry allocates (no allocation)."""
+    lib = _lib.load()
+    out = ctypes.c_size_t()
+    flags = _lib.SPECT_PLAN_LOW_MEMORY if low_memory else 0
+    _lib.check(lib.spect_plan_bytes(int(nx), int(nx), int(nz), int(nview), int(px), int(pz), int(nview_psf),
+                                    int(bool(separable)), flags, ctypes.byref(out)))
+    return out.value
+
+
 class SpectPlan:
     """The operator A of one geometry (Algorithm 1 inputs) on one GPU."""
 
@@ -174,9 +185,13 @@ class SpectPlan:
         return {"separable": bool(sep.value), "fused": bool(fused.value), "view_chunk": chunk.value,
                 "device_bytes": nbytes.value}
 
-    def check(self) -> None:
-        """Synchronise and raise SpectError(SPECT_ETIMEOUT) if a bounded device wait ran out."""
-        _lib.check(self.lib.spect_plan_check(self.handle))
+    def check(self, stream=None) -> None:
+        """Synchronise (the device, or only ``stream`` when given) and raise
+        SpectError(SPECT_ETIMEOUT) if a bounded device wait ran out."""
+        if stream is not None:
+            _lib.check(self.lib.spect_plan_check_stream(self.handle, _stream_handle(stream)))
+        else:
+            _lib.check(self.lib.spect_plan_check(self.handle))
 
     def profile(self, enable: bool = True) -> None:
         """Bracket every later kernel launch with CUDA events on its stream."""
@@ -189,6 +204,13 @@ class SpectPlan:
         ms = (ctypes.c_double * n)()
         _lib.check(self.lib.spect_profile_read(self.handle, la, ms, int(bool(reset))))
         return {k: (la[i], ms[i]) for i, k in enumerate(_lib.KERNEL_CLASSES)}
+
+    def release(self, stream) -> None:
+        """Free the plan after the work already enqueued on ``stream``, without
+        waiting for the device (all of the plan's work must be on ``stream``)."""
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            h, self.handle = self.handle, None
+            _lib.check(self.lib.spect_plan_release(h, _stream_handle(stream)))
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:

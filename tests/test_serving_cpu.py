@@ -1,0 +1,55 @@
+"""Scheduler of the reconstruction server on a simulated device (no GPU):
+admission by the device-memory budget, FIFO order, immediate retirement, and
+the comparison with one-at-a-time processing."""
+import numpy as np
+import pytest
+
+from paper_2301_09710_gb300.serving import FakeExecutor, Request, serve, serve_plain
+
+
+def _req(rid, arrival, nx=8, nz=4, nview=4, niter=3):
+    z = np.zeros((nz, nx, nx), np.float32)
+    return Request(rid, arrival, nx, nz, nview, niter, z, np.zeros((1, nx, 1), np.float32),
+                   np.zeros((1, nx, 1), np.float32), np.zeros((nview, nz, nx), np.float32))
+
+
+def test_admission_respects_memory_budget_and_completes_everything():
+    reqs = [_req(i, 0.001 * i) for i in range(10)]
+    per = FakeExecutor.plan_bytes(reqs[0])
+    ex = FakeExecutor(iter_cost=0.01)
+    st = serve(reqs, ex, mem_budget=3 * per, max_active=8)
+    assert [r.rid for r in st.results] == list(range(10))
+    assert st.peak_bytes <= 3 * per and st.peak_active == 3
+    for r in st.results:
+        assert r.admitted >= r.arrival and r.done >= r.admitted + 3 * 0.01 - 1e-9
+
+
+def test_slots_limit_concurrency():
+    reqs = [_req(i, 0.0) for i in range(6)]
+    st = serve(reqs, FakeExecutor(), mem_budget=1 << 40, max_active=2)
+    assert st.peak_active == 2
+
+
+def test_fifo_admission_under_pressure():
+    reqs = [_req(0, 0.0, niter=10), _req(1, 0.001, nx=16), _req(2, 0.002)]
+    per_small = FakeExecutor.plan_bytes(reqs[0])
+    ex = FakeExecutor(iter_cost=0.01)
+    # budget: the big request (16x16) does not fit beside the first one; the
+    # third (small, would fit) must not overtake it
+    st = serve(reqs, ex, mem_budget=per_small + FakeExecutor.plan_bytes(reqs[1]) - 1, max_active=4)
+    starts = [e for e in ex.log if e[0] == "start"]
+    assert [e[1] for e in starts] == [0, 1, 2]
+
+
+def test_request_beyond_budget_is_refused():
+    with pytest.raises(ValueError, match="budget"):
+        serve([_req(0, 0.0, nx=64)], FakeExecutor(), mem_budget=10)
+
+
+def test_concurrency_beats_one_at_a_time_on_the_simulated_device():
+    rng = np.random.default_rng(0)
+    arr = np.cumsum(rng.exponential(0.005, 30))
+    reqs = [_req(i, float(a), niter=int(rng.integers(4, 9))) for i, a in enumerate(arr)]
+    served = serve(reqs, FakeExecutor(iter_cost=0.01), mem_budget=1 << 40, max_active=8).summary()
+    plain = serve_plain(reqs, FakeExecutor(iter_cost=0.01)).summary()
+    assert served["p99_s"] < plain["p99_s"] and served["recon_per_s"] > plain["recon_per_s"]
