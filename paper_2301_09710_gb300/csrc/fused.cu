@@ -20,6 +20,8 @@
 //    into blurred-adjoint planes times mubar (the t slab, [v][j][i][k]); a
 //    gather kernel then sums sum_l sum_p W_l(p;q) t_l(p,k) per destination voxel
 //    q over fixed-length adjacency lists (weights bitwise those of A).
+#include <cstdlib>
+
 #include "spect_internal.cuh"
 
 namespace spect {
@@ -223,28 +225,39 @@ struct Sep {
 constexpr int kFusedThreads = 640;
 
 // Shared-memory plan of a fused kernel, computed identically on host and device.
+// Planes wider than shared memory allows are cut into nT column tiles of TI
+// detector columns (TI a multiple of CX); a tile carries C halo columns on
+// each side, so every tile is blurred independently.  nT = 1 is the untiled
+// case (TI = nib*CX >= nx).
 struct FusedDims {
-    int wp;     // W row pitch (odd, >= nib*CX + 2*C)
-    int warea;  // floats reserved for W (multiple of 4, keeps U 16-byte aligned)
+    int wp;     // W row pitch of one tile image (odd, >= TI + 2*C)
+    int warea;  // floats of one tile image, nz x wp (multiple of 4, keeps U 16-byte aligned)
+    int parea;  // floats of one plane's tile images in the slab, nT x warea
     int kpu;    // U row pitch (>= nkb*CZ + 2*ZH, multiple of 4, pitch/4 odd)
     int nib, nkb;
+    int TI, nT; // tile width in columns (multiple of CX), tiles per plane
+    int wpf;    // row pitch of the untiled plane image (odd, >= nib*CX + 2*C)
+    int farea;  // floats of the untiled plane image (the rotation kernel's shared memory)
+    int urows;  // rows of U / ACC / MB per tile: min(TI, nx)
+    int vrows;  // detector rows a tile's k-adjoint needs: min(nx, TI + 2*C)
+    int marea;  // floats of an attenuation tile, urows*nz rounded up to 4
     int J, G;   // depth planes per block, depth groups
     int ps;     // plane stride of the attenuation cache / slab (nx*nz rounded up to 4)
     int ts;     // rotation table block per (view, row): 5*nx rounded up to 4
     int apc;    // accumulator row pitch (>= nkb*CZ, multiple of 4, pitch/4 odd)
 };
 
-__host__ __device__ inline size_t fwd_smem_floats(const FusedDims& d, int nx, int nz, int PT)
+__host__ __device__ inline size_t fwd_smem_floats(const FusedDims& d, int nz, int PT)
 {
     // W x2 | U | taps J x (FX,FZ) | ACC | folded edge taps J x 2 x nz | 2 mbarriers
-    return 2 * (size_t)d.warea + (size_t)nx * d.kpu + 2 * (size_t)PT * d.J + (size_t)nx * d.apc +
+    return 2 * (size_t)d.warea + (size_t)d.urows * d.kpu + 2 * (size_t)PT * d.J + (size_t)d.urows * d.apc +
            2 * (size_t)d.J * nz + 10;
 }
 
-__host__ __device__ inline size_t adj_smem_floats(const FusedDims& d, int nx, int PT)
+__host__ __device__ inline size_t adj_smem_floats(const FusedDims& d, int PT)
 {
     // Zb | V | MB x2 | taps J x (FX[3],FZ[3]) | 2 mbarriers
-    return (size_t)d.warea + (size_t)nx * d.kpu + 2 * (size_t)d.ps + 6 * (size_t)PT * d.J + 8;
+    return (size_t)d.warea + (size_t)d.vrows * d.kpu + 2 * (size_t)d.marea + 6 * (size_t)PT * d.J + 8;
 }
 
 template <int P>
@@ -294,10 +307,13 @@ __device__ __forceinline__ void flag_timeout(int* err)
 // rows i with lanes over k, so the table entry and the four corner pointers
 // are warp-uniform and every gather is a coalesced run along k (96 k per
 // pass, 30 independent loads per lane in flight).  The plane is
-// assembled in shared memory exactly as the blur kernel wants it -- W[k][C+i]
-// with replicate halo columns and odd pitch wp -- and leaves with one TMA bulk
-// store, so the blur kernel can bring it back with one bulk load.
+// assembled in shared memory as the blur kernel wants it -- W[k][C+i] with
+// replicate halo columns and odd pitch -- and leaves with one TMA bulk store,
+// so the blur kernel can bring it back with one bulk load.  A plane cut into
+// column tiles leaves instead as nT tile images W_t[k][c] = W[k][t*TI + c],
+// c < TI + 2C, written with coalesced stores.
 // ----------------------------------------------------------------------------
+
 constexpr int kRotThreads = 512;
 
 template <int P>
@@ -314,6 +330,7 @@ __global__ void __launch_bounds__(kRotThreads, 2) k_rot_fwd(Geometry g, FusedDim
     constexpr int NW = kRotThreads / 32;
     const int j = blockIdx.x, v = blockIdx.y, l = l0 + v;
     const int pln = nx * nz;
+    const int wp = d.wpf;
     const int wcols = d.nib * Sep<P>::CX + 2 * C;
     const float* tab = rtab + ((size_t)l * ny + j) * d.ts;
     const float4* TW = reinterpret_cast<const float4*>(tab);
@@ -348,7 +365,7 @@ __global__ void __launch_bounds__(kRotThreads, 2) k_rot_fwd(Geometry g, FusedDim
             for (int q = 0; q < 3; ++q) {
                 const int k = k0 + 32 * q + lane;
                 if (k < nz) {
-                    float* wr = S + k * d.wp + C;
+                    float* wr = S + k * wp + C;
                     float va = wa.x * xa[q][0];
                     va = fmaf(wa.y, xa[q][1], va);
                     va = fmaf(wa.z, xa[q][2], va);
@@ -374,20 +391,34 @@ __global__ void __launch_bounds__(kRotThreads, 2) k_rot_fwd(Geometry g, FusedDim
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        fence_proxy_async_smem();
-        tma_store_1d(wsl + ((size_t)v * ny + j) * d.warea, S, (unsigned)d.warea * 4u);
-        tma_store_wait_all();
+    float* dst = wsl + ((size_t)v * ny + j) * d.parea;
+    if (d.nT == 1) {
+        if (threadIdx.x == 0) {
+            fence_proxy_async_smem();
+            tma_store_1d(dst, S, (unsigned)d.parea * 4u);
+            tma_store_wait_all();
+        }
+        return;
+    }
+    // tile images: row k of tile t is W[k][t*TI .. t*TI + TI + 2C), cut at
+    // the end of the plane's row (the blur never reads past it)
+    for (int r = warp; r < d.nT * nz; r += NW) {
+        const int t = r / nz, k = r - t * nz;
+        const int tw = min(d.TI + 2 * C, wcols - t * d.TI);
+        const float* src = S + k * wp + t * d.TI;
+        float* out = dst + (size_t)t * d.warea + (size_t)k * d.wp;
+        for (int c = lane; c < tw; c += 32) out[c] = src[c];
     }
 }
 
 // ----------------------------------------------------------------------------
-// Forward blur + depth sum: one block per (view, group of J depth planes).
+// Forward blur + depth sum: one block per (depth group of J planes, view,
+// column tile).
 // Rotated planes arrive by TMA into a double buffer (plane j+2 is requested as
 // soon as plane j's i-pass has read its buffer); per plane the i-pass writes U
 // (k halos by warp shuffles), the k-pass accumulates into ACC.
 // ----------------------------------------------------------------------------
-template <int P>
+template <int P, bool TILED>
 __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, FusedDims d,
                                                                      const float* __restrict__ wsl,
                                                                      const float* __restrict__ fx,
@@ -400,18 +431,23 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     float* WB = sm;                                    // [2][warea]
     float* U = WB + 2 * (size_t)d.warea;
-    float* TAP = U + (size_t)nx * d.kpu;               // [J][FX PT | FZ PT], every plane of the group
-    float* ACC = TAP + 2 * PT * (size_t)d.J;           // nx x apc, [i][k]
-    float* FOLD = ACC + (size_t)nx * d.apc;             // [J][2][nz] folded edge taps of the k-pass
+    float* TAP = U + (size_t)d.urows * d.kpu;          // [J][FX PT | FZ PT], every plane of the group
+    float* ACC = TAP + 2 * PT * (size_t)d.J;           // urows x apc, [i - i0][k]
+    float* FOLD = ACC + (size_t)d.urows * d.apc;        // [J][2][nz] folded edge taps of the k-pass
     uint64_t* bar = reinterpret_cast<uint64_t*>(FOLD + ((2 * (size_t)d.J * nz + 1) & ~(size_t)1));
     const int tid = threadIdx.x;
     constexpr int T = kFusedThreads;
     const int grp = blockIdx.x, v = blockIdx.y, l = l0 + v;
+    // this tile's columns (untiled: the whole plane, constants folded at compile time)
+    const int i0 = TILED ? (int)blockIdx.z * d.TI : 0;
+    const int ti = TILED ? min(d.TI, nx - i0) : nx;
+    const int nibt = TILED ? (ti + CX - 1) / CX : d.nib;
     const int lp = g.nvp == 1 ? 0 : l;
     const int j_begin = grp * d.J, j_end = min(ny, j_begin + d.J);
     const int ox = (P - g.px) / 2, oz = (P - g.pz) / 2;  // zero-padding offsets of the taps
     const int pln = nx * nz;
-    const float* wv = wsl + (size_t)v * ny * d.warea;
+    // tile blockIdx.z of plane j sits at wv + j * parea
+    const float* wv = wsl + (size_t)v * ny * d.parea + (size_t)blockIdx.z * d.warea;
 
     // taps of every plane of the group (zero-padded to P, centred)
     for (int e = tid; e < (j_end - j_begin) * PT; e += T) {
@@ -420,15 +456,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
         TAP[jj * 2 * PT + a] = (ax >= 0 && ax < g.px) ? __ldg(fx + ((size_t)lp * ny + j) * g.px + ax) : 0.f;
         TAP[jj * 2 * PT + PT + a] = (az >= 0 && az < g.pz) ? __ldg(fz + ((size_t)lp * ny + j) * g.pz + az) : 0.f;
     }
-    for (int e = tid; e < nx * d.apc; e += T) ACC[e] = 0.f;
-    for (int e = tid; e < nx * d.kpu; e += T) U[e] = 0.f;  // zero k-halo columns (never written again)
+    for (int e = tid; e < d.urows * d.apc; e += T) ACC[e] = 0.f;
+    for (int e = tid; e < d.urows * d.kpu; e += T) U[e] = 0.f;  // zero k-halo columns (never written again)
     if (tid == 0) {
         mbar_init(bar, 1);
         mbar_init(bar + 1, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        tma_load_1d(WB, wv + (size_t)j_begin * d.warea, (unsigned)d.warea * 4u, bar);
+        tma_load_1d(WB, wv + (size_t)j_begin * d.parea, (unsigned)d.warea * 4u, bar);
         if (j_begin + 1 < j_end)
-            tma_load_1d(WB + d.warea, wv + (size_t)(j_begin + 1) * d.warea, (unsigned)d.warea * 4u, bar + 1);
+            tma_load_1d(WB + d.warea, wv + (size_t)(j_begin + 1) * d.parea, (unsigned)d.warea * 4u, bar + 1);
     }
     __syncthreads();
     // replicate padding along k, folded: output k takes U(0) * sum_{b > k+C} fz(b)
@@ -455,23 +491,23 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
 
         // i-pass: U(i,k) = sum_a fx(a) w(clamp(i-a+cx), k); lanes over k
         if (ok) {
-            for (int it = tid; it < nz * d.nib; it += T) {
+            for (int it = tid; it < nz * nibt; it += T) {
                 const int ib = it / nz, k = it - ib * nz;
-                const int i0 = ib * CX;
-                const float* wr = W + k * d.wp + i0;
+                const int li = ib * CX;  // first column of this run, relative to the tile
+                const float* wr = W + k * d.wp + li;
                 float win[CX + P - 1];
 #pragma unroll
                 for (int m = 0; m < CX + P - 1; ++m) win[m] = wr[m];
                 float o[CX];
                 fir<P, CX, -1, P - 1>(FX, win, o);
-                float* ur = U + i0 * d.kpu + ZH + k;
-                if (i0 + CX <= nx) {
+                float* ur = U + li * d.kpu + ZH + k;
+                if (li + CX <= ti) {
 #pragma unroll
                     for (int c = 0; c < CX; ++c) ur[c * d.kpu] = o[c];
                 } else {
 #pragma unroll
                     for (int c = 0; c < CX; ++c)
-                        if (i0 + c < nx) ur[c * d.kpu] = o[c];
+                        if (li + c < ti) ur[c * d.kpu] = o[c];
                 }
             }
         }
@@ -487,15 +523,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
         // which has the fewest halo rows below)
         if (tid == T - 32 && j + 2 < j_end) {
             fence_proxy_async_smem();
-            tma_load_1d(WB + b * (size_t)d.warea, wv + (size_t)(j + 2) * d.warea, (unsigned)d.warea * 4u, bar + b);
+            tma_load_1d(WB + b * (size_t)d.warea, wv + (size_t)(j + 2) * d.parea, (unsigned)d.warea * 4u, bar + b);
         }
 
         // k-pass into the depth-sum accumulators: lanes over i; zero-padded
         // FIR plus the folded replicate-padding terms on the edge rows
         const float* fold_lo = FOLD + (j - j_begin) * 2 * nz;
         const float* fold_hi = fold_lo + nz;
-        for (int it = tid; it < nx * d.nkb; it += T) {
-            const int kb = it / nx, i = it - kb * nx;
+        for (int it = tid; it < ti * d.nkb; it += T) {
+            const int kb = it / ti, i = it - kb * ti;  // i relative to the tile
             const float* ur = U + i * d.kpu;
             float win[WZ];
             load_window_f4<P>(ur + kb * CZ, win);
@@ -524,11 +560,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
         __syncthreads();
     }
 
-    // partial depth sums of this group: part[grp][l][k][i]
-    float* pout = part + ((size_t)grp * g.nview + l) * pln;
-    for (int e = tid; e < pln; e += T) {
-        const int k = e / nx, i = e - k * nx;
-        pout[e] = ACC[i * d.apc + k];
+    // partial depth sums of this group: part[grp][l][k][i], this tile's columns
+    float* pout = part + ((size_t)grp * g.nview + l) * pln + i0;
+    for (int e = tid; e < nz * ti; e += T) {
+        const int k = e / ti, i = e - k * ti;
+        pout[(size_t)k * nx + i] = ACC[i * d.apc + k];
     }
 }
 
@@ -557,7 +593,7 @@ __global__ void k_fwd_reduce(const float* __restrict__ part, int G, size_t nproj
 //       in place with t = wbar * mubar, and leaves for the slab by a TMA bulk
 //       store; the buffer of plane j+1 is loaded while plane j is computed.
 // ============================================================================
-template <int P>
+template <int P, bool TILED>
 __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, FusedDims d, int cls_z,
                                                                      const float* __restrict__ vin,
                                                                      const float* __restrict__ mubar,
@@ -571,19 +607,31 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     float* Zb = sm;
     float* V = Zb + d.warea;
-    float* MB = V + (size_t)nx * d.kpu;  // [2][ps]
-    float* TAP = MB + 2 * (size_t)d.ps;  // [J][FX 3 classes | FZ 3 classes] x PT, every plane of the group
+    float* MB = V + (size_t)d.vrows * d.kpu;  // [2][marea]
+    float* TAP = MB + 2 * (size_t)d.marea;    // [J][FX 3 classes | FZ 3 classes] x PT, every plane of the group
     uint64_t* bar = reinterpret_cast<uint64_t*>(TAP + 6 * PT * (size_t)d.J);
     const int tid = threadIdx.x;
     constexpr int T = kFusedThreads;
     const int grp = blockIdx.x, v = blockIdx.y, l = l0 + v;
+    // output columns [i0, i0 + ti); their i-adjoint reads detector rows [vlo, vhi)
+    // (untiled: the whole plane, with the constants folded at compile time)
+    const int i0 = TILED ? (int)blockIdx.z * d.TI : 0;
+    const int ti = TILED ? min(d.TI, nx - i0) : nx;
+    const int vlo = TILED ? max(0, i0 - C) : 0;
+    const int nvr = TILED ? min(nx, i0 + d.TI + C) - vlo : nx;
+    const int nibt = TILED ? (ti + CX - 1) / CX : d.nib;
+    const int zoff = C + vlo - i0;       // Zb column of detector row vlo
+    const int last_col = nx - 1 - i0;    // tile-relative position of column nx-1
+    const bool first_tile = i0 == 0;
+    // attenuation / t tile: columns [i0, i0 + ti) of a plane are one contiguous run
+#define SPECT_MBYTES ((unsigned)(((size_t)ti * nz + 3) & ~(size_t)3) * 4u)
     const int lp = g.nvp == 1 ? 0 : l;
     const int j_begin = grp * d.J, j_end = min(ny, j_begin + d.J);
     const int ox = (P - g.px) / 2, oz = (P - g.pz) / 2;
     const size_t nrow = (size_t)g.nvp * ny;
     const int pln = nx * nz;
-    const float* mub = mubar + ((size_t)l * ny) * d.ps;
-    float* tsl = slab + ((size_t)v * ny) * d.ps;
+    const float* mub = mubar + ((size_t)l * ny) * d.ps + (size_t)i0 * nz;
+    float* tsl = slab + ((size_t)v * ny) * d.ps + (size_t)i0 * nz;
 
     // edge-class taps of every plane of the group
     for (int e = tid; e < (j_end - j_begin) * 3 * PT; e += T) {
@@ -597,18 +645,18 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
     }
 
     // stage the detector plane v(:,:,l) transposed, zero outside the detector
-    for (int e = tid; e < nx * d.kpu; e += T) V[e] = 0.f;
+    for (int e = tid; e < d.vrows * d.kpu; e += T) V[e] = 0.f;
     for (int e = tid; e < d.warea; e += T) Zb[e] = 0.f;
     if (tid == 0) {
         mbar_init(bar, 1);
         mbar_init(bar + 1, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        tma_load_1d(MB, mub + (size_t)j_begin * d.ps, (unsigned)d.ps * 4u, bar);
+        tma_load_1d(MB, mub + (size_t)j_begin * d.ps, SPECT_MBYTES, bar);
     }
     __syncthreads();
-    for (int e = tid; e < pln; e += T) {
-        const int k = e / nx, i = e - k * nx;
-        V[i * d.kpu + ZH + k] = vin[(size_t)l * pln + e];
+    for (int e = tid; e < nz * nvr; e += T) {
+        const int k = e / nvr, r = e - k * nvr;
+        V[r * d.kpu + ZH + k] = vin[(size_t)l * pln + (size_t)k * nx + vlo + r];
     }
     __syncthreads();
 
@@ -620,9 +668,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
         // k-adjoint: Zb[k][C+i] = sum_b' fz~(b') v(i, k+b'-cz), lanes over i.
         // The first and last detector rows, where replicate padding folds
         // taps together, take their edge-class taps instead of the interior ones.
-        for (int it = tid; it < nx * d.nkb; it += T) {
-            const int kb = it / nx, i = it - kb * nx;
-            const float* vr = V + i * d.kpu;
+        for (int it = tid; it < nvr * d.nkb; it += T) {
+            const int kb = it / nvr, r = it - kb * nvr;  // detector row vlo + r
+            const float* vr = V + r * d.kpu;
             float win[WZ];
             load_window_f4<P>(vr + kb * CZ, win);
             float o[CZ];
@@ -643,7 +691,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
                 const float* vv = vr + (nz - 1) - C + ZH;
                 for (int bb = 0; bb < P; ++bb) e_last = fmaf(f[bb], vv[bb], e_last);
             }
-            float* zc = Zb + C + i;
+            float* zc = Zb + zoff + r;
             if (k0 + CZ <= nz && !last) {
 #pragma unroll
                 for (int c = 0; c < CZ; ++c) zc[(k0 + c) * d.wp] = o[c];
@@ -658,39 +706,39 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
         // k-adjoint to read it; it now receives the next plane's attenuation
         if (tid == 0 && j + 1 < j_end) {
             tma_store_wait_read<0>();
-            tma_load_1d(MB + (b ^ 1) * (size_t)d.ps, mub + (size_t)(j + 1) * d.ps, (unsigned)d.ps * 4u, bar + (b ^ 1));
+            tma_load_1d(MB + (b ^ 1) * (size_t)d.marea, mub + (size_t)(j + 1) * d.ps, SPECT_MBYTES, bar + (b ^ 1));
         }
 
         // i-adjoint times mubar, in place in MB[b]; lanes over k
-        float* mb = MB + b * (size_t)d.ps;
+        float* mb = MB + b * (size_t)d.marea;
         const bool ok = mbar_wait_bounded(bar + b, phase[b]);
         phase[b] ^= 1u;
         if (ok) {
-            for (int it = tid; it < nz * d.nib; it += T) {
+            for (int it = tid; it < nz * nibt; it += T) {
                 const int ib = it / nz, k = it - ib * nz;
-                const int i0 = ib * CX;
-                const float* zr = Zb + k * d.wp + i0;
+                const int li = ib * CX;  // first column of this run, relative to the tile
+                const float* zr = Zb + k * d.wp + li;
                 float win[CX + P - 1];
 #pragma unroll
                 for (int m = 0; m < CX + P - 1; ++m) win[m] = zr[m];
                 float o[CX];
                 fir<P, CX, 1, 0>(FX, win, o);
                 // first / last detector column: edge-class taps (replicate-padding folds)
-                if (i0 == 0) {
+                if (first_tile && li == 0) {
                     const float* f = FX + PT;
                     float sacc = 0.f;
 #pragma unroll
                     for (int a = 0; a < P; ++a) sacc = fmaf(f[a], win[a], sacc);
                     o[0] = sacc;
                 }
-                const int cl = nx - 1 - i0;  // position of column nx-1 in this block
+                const int cl = last_col - li;  // position of column nx-1 in this run
                 const bool last = cl < CX;
                 float e_last = 0.f;
                 if (last) {
                     const float* f = FX + 2 * PT;
                     for (int a = 0; a < P; ++a) e_last = fmaf(f[a], zr[cl + a], e_last);
                 }
-                float* mp = mb + i0 * nz + k;
+                float* mp = mb + li * nz + k;
                 if (!last) {
 #pragma unroll
                     for (int c = 0; c < CX; ++c) mp[c * nz] = o[c] * mp[c * nz];
@@ -712,10 +760,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
         // t plane -> slab[v][j]
         if (tid == 0) {
             fence_proxy_async_smem();
-            tma_store_1d(tsl + (size_t)j * d.ps, mb, (unsigned)d.ps * 4u);
+            tma_store_1d(tsl + (size_t)j * d.ps, mb, SPECT_MBYTES);
         }
     }
     if (tid == 0) tma_store_wait_all();
+#undef SPECT_MBYTES
 }
 
 // x_t(q,k) (+)= sum_{v in chunk} sum_{e < MAXE} w_e t[v][p_e][k]
@@ -829,7 +878,7 @@ namespace {
 constexpr int kBuckets[] = {3, 5, 7, 9, 11, 13, 15, 17, 21, 25, 29, 33, 37};
 
 template <int P>
-FusedDims dims_for(const Geometry& g, int J)
+FusedDims dims_for(const Geometry& g, int J, int tiles)
 {
     using S = Sep<P>;
     FusedDims d;
@@ -837,8 +886,17 @@ FusedDims dims_for(const Geometry& g, int J)
     d.ts = (5 * g.nx + 3) & ~3;
     d.nib = (g.nx + S::CX - 1) / S::CX;
     d.nkb = (g.nz + S::CZ - 1) / S::CZ;
-    d.wp = (d.nib * S::CX + 2 * S::C) | 1;
+    tiles = tiles < 1 ? 1 : (tiles > d.nib ? d.nib : tiles);
+    d.TI = ((d.nib + tiles - 1) / tiles) * S::CX;
+    d.nT = (g.nx + d.TI - 1) / d.TI;
+    d.urows = d.TI < g.nx ? d.TI : g.nx;
+    d.vrows = d.TI + 2 * S::C < g.nx ? d.TI + 2 * S::C : g.nx;
+    d.marea = (d.urows * g.nz + 3) & ~3;
+    d.wp = (d.TI + 2 * S::C) | 1;
     d.warea = (g.nz * d.wp + 3) & ~3;
+    d.parea = d.nT * d.warea;
+    d.wpf = (d.nib * S::CX + 2 * S::C) | 1;
+    d.farea = (g.nz * d.wpf + 3) & ~3;
     int kpu = d.nkb * S::CZ + 2 * S::ZH;
     kpu = (kpu + 3) & ~3;
     if (((kpu / 4) & 1) == 0) kpu += 4;
@@ -854,39 +912,52 @@ FusedDims dims_for(const Geometry& g, int J)
 template <int P>
 size_t smem_fwd(const Geometry& g, const FusedDims& d)
 {
-    return fwd_smem_floats(d, g.nx, g.nz, Sep<P>::PT) * sizeof(float);
+    return fwd_smem_floats(d, g.nz, Sep<P>::PT) * sizeof(float);
 }
 
 template <int P>
 size_t smem_adj(const Geometry& g, const FusedDims& d)
 {
-    return adj_smem_floats(d, g.nx, Sep<P>::PT) * sizeof(float);
+    (void)g;
+    return adj_smem_floats(d, Sep<P>::PT) * sizeof(float);
 }
 
+// The fewest column tiles with which the rotation, blur and adjoint kernels
+// fit `limit` bytes of shared memory (and every bulk copy stays below the
+// mbarrier's 2^20-byte transaction count); 0 when none does.
 template <int P>
-bool fits(const Geometry& g, size_t limit)
+int tiles_that_fit(const Geometry& g, size_t limit, int min_tiles)
 {
-    const FusedDims d = dims_for<P>(g, 8);
-    return smem_fwd<P>(g, d) <= limit && smem_adj<P>(g, d) <= limit && (size_t)d.ps * 4 < (1u << 20);
+    const int nib = (g.nx + Sep<P>::CX - 1) / Sep<P>::CX;
+    int last_nt = 0;
+    for (int t = min_tiles < 1 ? 1 : min_tiles; t <= nib; ++t) {
+        const FusedDims d = dims_for<P>(g, 8, t);
+        if (d.nT == last_nt) continue;  // same tile width as a smaller request
+        last_nt = d.nT;
+        if (smem_fwd<P>(g, d) <= limit && smem_adj<P>(g, d) <= limit && (size_t)d.farea * 4 <= limit &&
+            (size_t)d.marea * 4 < (1u << 20))
+            return d.nT;
+    }
+    return 0;
 }
 
 template <int P>
 cudaError_t fwd_launch(const spect_plan_s& Pl, const float* xt, int l0, int nv, cudaStream_t st)
 {
-    const FusedDims d = dims_for<P>(Pl.g, Pl.fused_J);
+    const FusedDims d = dims_for<P>(Pl.g, Pl.fused_J, Pl.fused_nT);
     const size_t smem = smem_fwd<P>(Pl.g, d);
-    cudaError_t e = cudaFuncSetAttribute(k_fwd_sep_fused<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = d.nT > 1 ? k_fwd_sep_fused<P, true> : k_fwd_sep_fused<P, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_fwd_sep_fused<P><<<dim3(d.G, nv), kFusedThreads, smem, st>>>(Pl.g, d, Pl.slab, Pl.fx, Pl.fz, Pl.part, l0,
-                                                                    Pl.err);
+    kern<<<dim3(d.G, nv, d.nT), kFusedThreads, smem, st>>>(Pl.g, d, Pl.slab, Pl.fx, Pl.fz, Pl.part, l0, Pl.err);
     return cudaGetLastError();
 }
 
 template <int P>
 cudaError_t rot_launch(const spect_plan_s& Pl, const float* xt, int l0, int nv, cudaStream_t st)
 {
-    const FusedDims d = dims_for<P>(Pl.g, Pl.fused_J);
-    const size_t smem = (size_t)d.warea * sizeof(float);
+    const FusedDims d = dims_for<P>(Pl.g, Pl.fused_J, Pl.fused_nT);
+    const size_t smem = (size_t)d.farea * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_rot_fwd<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_rot_fwd<P><<<dim3(Pl.g.ny, nv), kRotThreads, smem, st>>>(Pl.g, d, Pl.rtab, xt, Pl.mubar, Pl.slab, l0);
@@ -896,31 +967,38 @@ cudaError_t rot_launch(const spect_plan_s& Pl, const float* xt, int l0, int nv, 
 template <int P>
 cudaError_t adj_launch(const spect_plan_s& Pl, const float* v, int l0, int nv, cudaStream_t st)
 {
-    const FusedDims d = dims_for<P>(Pl.g, Pl.adj_J);
+    const FusedDims d = dims_for<P>(Pl.g, Pl.adj_J, Pl.fused_nT);
     const size_t smem = smem_adj<P>(Pl.g, d);
-    cudaError_t e = cudaFuncSetAttribute(k_adj_sep_fused<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = d.nT > 1 ? k_adj_sep_fused<P, true> : k_adj_sep_fused<P, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_adj_sep_fused<P><<<dim3(d.G, nv), kFusedThreads, smem, st>>>(Pl.g, d, Pl.cls_z, v, Pl.mubar, Pl.fx_adj,
-                                                                    Pl.fz_adj, Pl.slab, l0, Pl.err);
+    kern<<<dim3(d.G, nv, d.nT), kFusedThreads, smem, st>>>(Pl.g, d, Pl.cls_z, v, Pl.mubar, Pl.fx_adj, Pl.fz_adj,
+                                                           Pl.slab, l0, Pl.err);
     return cudaGetLastError();
 }
 }  // namespace
 
-int fused_bucket(const Geometry& g, size_t smem_limit)
+int fused_bucket(const Geometry& g, size_t smem_limit, int* tiles)
 {
     const int p = g.px > g.pz ? g.px : g.pz;
+    *tiles = 0;
+    // SPECT_FUSED_TILES: at least this many column tiles (testing and tuning;
+    // results are bitwise those of the untiled kernels)
+    const char* env = getenv("SPECT_FUSED_TILES");
+    const int min_tiles = env ? atoi(env) : 1;
     for (int b : kBuckets) {
         if (b < p) continue;
-        bool ok = false;
+        int nt = 0;
         switch (b) {
 #define SPECT_FITS(B) \
-    case B: ok = fits<B>(g, smem_limit); break;
+    case B: nt = tiles_that_fit<B>(g, smem_limit, min_tiles); break;
             SPECT_FITS(3) SPECT_FITS(5) SPECT_FITS(7) SPECT_FITS(9) SPECT_FITS(11) SPECT_FITS(13) SPECT_FITS(15)
             SPECT_FITS(17) SPECT_FITS(21) SPECT_FITS(25) SPECT_FITS(29) SPECT_FITS(33) SPECT_FITS(37)
 #undef SPECT_FITS
             default: break;
         }
-        return ok ? b : 0;
+        *tiles = nt;
+        return nt > 0 ? b : 0;
     }
     return 0;
 }
@@ -955,16 +1033,28 @@ cudaError_t launch_fused_rotate(const spect_plan_s& P, const float* xt, int l0, 
     SPECT_DISPATCH(rot_launch, P, xt, l0, nv, st)
 }
 
-// floats per view of the work slab the fused path needs (rotated planes or t planes)
+namespace {
+template <int P>
+size_t plane_area(const spect_plan_s& Pl)
+{
+    return (size_t)dims_for<P>(Pl.g, Pl.fused_J, Pl.fused_nT).parea;
+}
+}  // namespace
+
+// floats per view of the work slab the fused path needs (rotated tile images or t planes)
 size_t fused_slab_per_view(const spect_plan_s& P)
 {
-    const int p = P.bucket;
-    int C = (p - 1) / 2;
-    const int nib = (P.g.nx + 15) / 16;
-    const int wp = (nib * 16 + 2 * C) | 1;
-    const size_t warea = ((size_t)P.g.nz * wp + 3) & ~(size_t)3;
+    size_t parea = 0;
+    switch (P.bucket) {
+#define SPECT_AREA(B) \
+    case B: parea = plane_area<B>(P); break;
+        SPECT_AREA(3) SPECT_AREA(5) SPECT_AREA(7) SPECT_AREA(9) SPECT_AREA(11) SPECT_AREA(13) SPECT_AREA(15)
+        SPECT_AREA(17) SPECT_AREA(21) SPECT_AREA(25) SPECT_AREA(29) SPECT_AREA(33) SPECT_AREA(37)
+#undef SPECT_AREA
+        default: break;
+    }
     const size_t ps = ((size_t)P.g.nx * P.g.nz + 3) & ~(size_t)3;
-    return (size_t)P.g.ny * (warea > ps ? warea : ps);
+    return (size_t)P.g.ny * (parea > ps ? parea : ps);
 }
 
 cudaError_t launch_fused_adjoint(const spect_plan_s& P, const float* v, int l0, int nv, cudaStream_t st)

@@ -378,7 +378,7 @@ spect_status spect_plan_bytes(int nx, int ny, int nz, int nview, int px, int pz,
     P.cls_x = 3;
     P.cls_z = nz >= 2 ? 3 : 1;
     if (P.separable && !(flags & SPECT_PLAN_LOW_MEMORY)) {
-        P.bucket = spect::fused_bucket(g, (size_t)smem_optin);
+        P.bucket = spect::fused_bucket(g, (size_t)smem_optin, &P.fused_nT);
         P.fast = P.bucket > 0;
     }
     *bytes = plan_bytes_bound(P);
@@ -456,7 +456,7 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
         P->pooled = pools != 0;
     }
     if (P->separable && !(flags & SPECT_PLAN_LOW_MEMORY)) {
-        P->bucket = spect::fused_bucket(g, (size_t)smem_optin);
+        P->bucket = spect::fused_bucket(g, (size_t)smem_optin, &P->fused_nT);
         P->fast = P->bucket > 0;
     }
     if (P->separable) {

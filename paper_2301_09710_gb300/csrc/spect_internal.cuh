@@ -79,6 +79,7 @@ struct spect_plan_s {
     int fast = 0;                // 1 when the fused kernels serve this plan
     int bucket = 0;              // padded tap count of the fused kernels
     int fused_J = 8;             // depth planes per fused forward block
+    int fused_nT = 1;            // column tiles per plane in the fused kernels
     int adj_J = 8;               // depth planes per fused adjoint block
     int adj_chunk = 0;           // views per adjoint pass (t slab sized to stay in L2)
     float* mubar = nullptr;      // nview * ny*nx*nz, [l][j][i][k]
@@ -303,7 +304,9 @@ cudaError_t launch_conv_adjoint(const spect_plan_s& P, const float* v, int l0, i
 cudaError_t launch_psf_variants(spect_plan_s& P, float* scratch, cudaStream_t st);
 int choose_sep_tile(const Geometry& g, int cls_z, size_t smem_limit);
 // fast path (fused.cu)
-int fused_bucket(const Geometry& g, size_t smem_limit);
+// PSF bucket (padded tap count) of the fused kernels for this geometry, 0 when
+// they do not fit; *tiles receives the column-tile count they need.
+int fused_bucket(const Geometry& g, size_t smem_limit, int* tiles);
 int fused_groups(const spect_plan_s& P);
 cudaError_t launch_transpose(const float* in, float* out, int R, int C, cudaStream_t st);
 cudaError_t launch_mubar_cache(const spect_plan_s& P, const float* mu_t, cudaStream_t st);

@@ -96,3 +96,32 @@ def test_config2_geometry_em_step_vs_oracle(prob, path):
     x1_o = oracle.em_step(x0, y, rbar, prob.mu, psf, prob.dy, ang, nthreads=4)
     assert_close(host(xg), x1_o, what="EM step, 128x128x80, 37x37 PSF")
     plan.close()
+
+
+@pytest.mark.parametrize("shape", [(192, 128, 128, 37, [37]), (160, 96, 120, 29, [0, 53])],
+                         ids=["192x192x128v128p37", "160x160x96v120p29"])
+def test_large_planes_sampled_views(shape):
+    """Planes too wide for one block's shared memory run on the column-tiled
+    fused kernels (the serving workload's large case); sampled views against
+    the oracle, adjointness over all views."""
+    nx, nz, nview, p, views = shape
+    x, mu, body = synthetic.small_phantom(nx, nz, 3)
+    fx, fz = synthetic.depth_psf_factors(nx, p, p, 1.5, 9.0, aniso=True)
+    prob = synthetic.Problem(x=x, mu=mu, dy=1.0, fx=fx, fz=fz, nview=nview, body=body, meta={})
+    ang = oracle.default_angles(nview)
+    plan = make_plan(prob, ang, "fused")
+    assert plan.info()["fused"]
+    psf = oracle_psf(prob, "fused")
+    xg = dev(x)
+    v = host(plan.forward(xg))
+    assert_close(v[views], oracle.forward(x, mu, psf, 1.0, ang[views]), what="A x sampled views")
+    rng = np.random.default_rng(8)
+    y = np.zeros(plan.proj_shape, np.float32)
+    y[views] = rng.uniform(0, 1, (len(views),) + plan.proj_shape[1:])
+    assert_close(host(plan.back(dev(y))), oracle.back(y[views], mu, psf, 1.0, ang[views]), what="A' y sampled views")
+    yy = rng.uniform(0, 1, plan.proj_shape).astype(np.float32)
+    lhs = np.vdot(v, yy.astype(np.float64))
+    rhs = np.vdot(x.astype(np.float64), host(plan.back(dev(yy))))
+    assert abs(lhs - rhs) <= ADJ_FP32 * abs(lhs)
+    plan.check()
+    plan.close()
