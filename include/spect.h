@@ -270,6 +270,55 @@ spect_status spect_plan_destroy(spect_plan plan);
 spect_status spect_plan_release(spect_plan plan, spect_stream stream);
 
 /*
+ * Launch-shape tuning of the fused kernels (the paper has no counterpart).
+ * fused_J / adj_J: depth planes per block of the forward / adjoint blur
+ * kernels (1..32); tiles: column tiles per plane (>= 1; the kernels use the
+ * nearest count that divides the plane into whole 16-column runs).  The plan
+ * grows its work slab and partial-sum buffer in stream order on `stream` when
+ * the shape needs more room.  Results stay within the FP32 tolerance of the
+ * oracle for every shape; A' is bitwise independent of the shape, A x depends
+ * on fused_J only through the grouping of its depth sum.
+ * Errors: SPECT_EINVAL, SPECT_EUNSUPPORTED (low-memory plan, or the shape
+ * does not fit shared memory), SPECT_ENOMEM, SPECT_ECUDA.
+ */
+spect_status spect_plan_set_tuning(spect_plan plan, int fused_J, int adj_J, int tiles, spect_stream stream);
+spect_status spect_plan_get_tuning(spect_plan plan, int* fused_J, int* adj_J, int* tiles);
+
+/*
+ * spect_plan_autotune -- time the fused kernels' candidate launch shapes
+ * (tiles x fused_J for A, tiles x adj_J for A') on this device with CUDA
+ * events on `stream` and keep the fastest; the choice is cached per geometry
+ * and device for the life of the process, so later plans of the same shape
+ * are set without timing.  Overwrites nothing the caller owns; synchronises
+ * `stream`.  Low-memory plans are left as they are (SPECT_OK).
+ */
+spect_status spect_plan_autotune(spect_plan plan, spect_stream stream);
+
+/*
+ * Batches: many plans of different sizes, view counts and PSF widths run
+ * their EM iterations as ONE CUDA graph launch (the paper has no
+ * counterpart).  spect_batch_em_step captures, per plan, the same kernel
+ * sequence spect_em_step would launch (niter iterations, transposes
+ * included), each plan on its own branch of the graph so the plans' kernels
+ * overlap on the device; the executable graph is cached and replayed while
+ * niter and the pointer arrays' contents stay the same.
+ *   plans        n distinct plans; the batch borrows them (destroy the batch
+ *                before its plans, and do not use the plans concurrently with
+ *                the batch).
+ *   x, y, rbar   HOST arrays of n DEVICE pointers (as spect_em_step; rbar may
+ *                be NULL, or hold NULL entries).
+ * Each plan's result is bitwise what spect_em_step gives for it alone.
+ * spect_batch_info: plans in the batch and kernels per graph launch.
+ * Errors: SPECT_EINVAL, SPECT_ECUDA (capture or graph failures).
+ */
+typedef struct spect_batch_s* spect_batch;
+spect_status spect_batch_create(spect_batch* out, const spect_plan* plans, int n);
+spect_status spect_batch_em_step(spect_batch batch, float* const* x, const float* const* y, const float* const* rbar,
+                                 int niter, spect_stream stream);
+spect_status spect_batch_info(spect_batch batch, int* n_plans, long long* kernels_per_launch);
+spect_status spect_batch_destroy(spect_batch batch);
+
+/*
  * spect_forward_static -- v = A x without any device allocation.
  *
  * For callers that cannot allocate device memory (code running while a CUDA

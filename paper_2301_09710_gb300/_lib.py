@@ -81,6 +81,21 @@ def load(path: str = LIB_PATH):
         lib.spect_forward_static.restype = st
         lib.spect_plan_check.argtypes = [vp]
         lib.spect_plan_check.restype = st
+        ip = ctypes.POINTER(i)
+        lib.spect_plan_set_tuning.argtypes = [vp, i, i, i, vp]
+        lib.spect_plan_set_tuning.restype = st
+        lib.spect_plan_get_tuning.argtypes = [vp, ip, ip, ip]
+        lib.spect_plan_get_tuning.restype = st
+        lib.spect_plan_autotune.argtypes = [vp, vp]
+        lib.spect_plan_autotune.restype = st
+        lib.spect_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), i]
+        lib.spect_batch_create.restype = st
+        lib.spect_batch_em_step.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp]
+        lib.spect_batch_em_step.restype = st
+        lib.spect_batch_info.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_longlong)]
+        lib.spect_batch_info.restype = st
+        lib.spect_batch_destroy.argtypes = [vp]
+        lib.spect_batch_destroy.restype = st
         lib.spect_plan_bytes.argtypes = [i, i, i, i, i, i, i, i, ctypes.c_uint, ctypes.POINTER(ctypes.c_size_t)]
         lib.spect_plan_bytes.restype = st
         lib.spect_plan_check_stream.argtypes = [vp, vp]

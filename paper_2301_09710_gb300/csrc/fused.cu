@@ -21,6 +21,7 @@
 //    gather kernel then sums sum_l sum_p W_l(p;q) t_l(p,k) per destination voxel
 //    q over fixed-length adjacency lists (weights bitwise those of A).
 #include <cstdlib>
+#include <type_traits>
 
 #include "spect_internal.cuh"
 
@@ -1001,6 +1002,28 @@ int fused_bucket(const Geometry& g, size_t smem_limit, int* tiles)
         return nt > 0 ? b : 0;
     }
     return 0;
+}
+
+// Column-tile count the fused kernels use when asked for `tiles` tiles with
+// depth groups of J (forward) and adj_J (adjoint) planes, or 0 when that
+// configuration does not fit `smem_limit` bytes of shared memory.
+int fused_tiles_fit(const Geometry& g, int bucket, int J, int adj_J, int tiles, size_t smem_limit)
+{
+    auto check = [&](auto tag) -> int {
+        constexpr int B = decltype(tag)::value;
+        const FusedDims df = dims_for<B>(g, J, tiles), da = dims_for<B>(g, adj_J, tiles);
+        const bool ok = smem_fwd<B>(g, df) <= smem_limit && smem_adj<B>(g, da) <= smem_limit &&
+                        (size_t)df.farea * 4 <= smem_limit && (size_t)df.marea * 4 < (1u << 20);
+        return ok ? df.nT : 0;
+    };
+    switch (bucket) {
+#define SPECT_TF(B) \
+    case B: return check(std::integral_constant<int, B>());
+        SPECT_TF(3) SPECT_TF(5) SPECT_TF(7) SPECT_TF(9) SPECT_TF(11) SPECT_TF(13) SPECT_TF(15)
+        SPECT_TF(17) SPECT_TF(21) SPECT_TF(25) SPECT_TF(29) SPECT_TF(33) SPECT_TF(37)
+#undef SPECT_TF
+        default: return 0;
+    }
 }
 
 int fused_groups(const spect_plan_s& P) { return (P.g.ny + P.fused_J - 1) / P.fused_J; }

@@ -7,7 +7,10 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "spect_internal.cuh"
@@ -296,6 +299,9 @@ spect_status ensure_sensitivity(spect_plan_s* P, cudaStream_t st)
     return SPECT_OK;
 }
 
+spect_status em_iterate(spect_plan_s* P, float* x, const float* y, const float* rbar, const float* u, float beta,
+                        int niter, cudaStream_t st);
+
 spect_status check_call(spect_plan P, const void* a, const void* b, const char* na, const char* nb)
 {
     if (!P) return fail(SPECT_EINVAL, "plan is NULL");
@@ -564,6 +570,7 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
     const size_t per_view = std::max(vol, P->fast ? spect::fused_slab_per_view(*P) : vol);
     P->chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)nview, budget / (per_view * sizeof(float))));
     PLAN_ALLOC(P->slab, per_view * (size_t)P->chunk, "work slab");
+    P->slab_cap = per_view * (size_t)P->chunk;
     // fused adjoint: all views of the slab in one pass by default (measured
     // faster than L2-sized passes); SPECT_ADJ_CHUNK sets fewer views per pass,
     // with a depth-group size that keeps about two blocks per SM (tuning)
@@ -590,6 +597,7 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
         PLAN_ALLOC(P->st, vol, "internal sensitivity");
         PLAN_ALLOC(P->ut, vol, "internal regulariser target");
         PLAN_ALLOC(P->part, nproj * (size_t)spect::fused_groups(*P), "depth-group partial sums");
+        P->part_cap = nproj * (size_t)spect::fused_groups(*P);
         // mu in the [j][i][k] layout (temporary, the slab serves as scratch)
         PLAN_TRY(spect::launch_transpose(P->mu, P->slab, nz, (int)nxy, st), "mu transpose launch");
         PLAN_TRY(spect::launch_mubar_cache(*P, P->slab, st), "attenuation cache launch");
@@ -681,6 +689,19 @@ spect_status spect_em_step_reg(spect_plan P, float* x, const float* y, const flo
     cudaStream_t st = (cudaStream_t)stream;
     r = ensure_sensitivity(P, st);
     if (r != SPECT_OK) return r;
+    return em_iterate(P, x, y, rbar, u, beta, niter, st);
+}
+
+}  // extern "C"
+
+namespace {
+
+// niter EM updates of x (Eqs. (7)-(8)) once the sensitivity is cached:
+// everything stream-ordered on st, no host synchronisation (capturable).
+spect_status em_iterate(spect_plan_s* P, float* x, const float* y, const float* rbar, const float* u, float beta,
+                        int niter, cudaStream_t st)
+{
+    spect_status r = SPECT_OK;
     if (niter == 0) return SPECT_OK;
     spect::EmArgs em;
     em.beta = beta > 0.f ? beta : 0.f;
@@ -713,6 +734,10 @@ spect_status spect_em_step_reg(spect_plan P, float* x, const float* y, const flo
     }
     return SPECT_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 spect_status spect_plan_check_stream(spect_plan P, spect_stream stream)
 {
@@ -771,6 +796,341 @@ spect_status spect_plan_info(spect_plan P, int* separable, int* fused, int* view
     if (fused) *fused = P->fast;
     if (view_chunk) *view_chunk = P->chunk;
     if (device_bytes) *device_bytes = P->bytes;
+    return SPECT_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// Tuning of the fused kernels' launch shapes, the autotuner, and batches of
+// plans run as one CUDA graph (the paper has no counterpart for any of these).
+// ============================================================================
+struct spect_batch_s {
+    std::vector<spect_plan_s*> plans;
+    std::vector<cudaStream_t> side;  // one capture branch per plan (round-robin when plans outnumber them)
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    cudaStream_t origin = nullptr;   // the capture's origin stream (the caller's may be the legacy stream)
+    // the instantiated graph and the arguments it was captured with
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void*> key;
+    long long graph_launches = 0;   // kernels per graph launch
+};
+
+namespace {
+
+spect_status realloc_floats(spect_plan_s* P, float** p, size_t* cap, size_t need, cudaStream_t st, const char* what)
+{
+    if (need <= *cap) return SPECT_OK;
+    float* q = nullptr;
+    cudaError_t e = raw_alloc(P, (void**)&q, need * sizeof(float), st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? SPECT_ENOMEM : SPECT_ECUDA,
+                    std::string("allocating ") + what + ": " + cudaGetErrorString(e));
+    }
+    if (((uintptr_t)q & 255) != 0) {
+        raw_free(P, q, st);
+        return fail(SPECT_ECUDA, std::string("allocation of ") + what + " is not 256-byte aligned");
+    }
+    raw_free(P, *p, st);
+    P->bytes += (need - *cap) * sizeof(float);
+    *p = q;
+    *cap = need;
+    return SPECT_OK;
+}
+
+// Set the fused kernels' depth-group sizes and column-tile count, growing the
+// work slab and the partial-sum buffer when the new shape needs more room.
+spect_status reconfigure(spect_plan_s* P, int J, int adj_J, int tiles, cudaStream_t st)
+{
+    if (!P->fast) return fail(SPECT_EUNSUPPORTED, "launch-shape tuning applies to the fused kernels only");
+    const Geometry& g = P->g;
+    if (J < 1 || J > 32 || adj_J < 1 || adj_J > 32 || tiles < 1)
+        return fail(SPECT_EINVAL, "fused_J and adj_J must be in [1, 32], tiles >= 1");
+    int dev = 0, smem = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SPECT_ECUDA, "device query failed");
+    }
+    const int nt = spect::fused_tiles_fit(g, P->bucket, J, adj_J, tiles, (size_t)smem);
+    if (nt == 0) return fail(SPECT_EUNSUPPORTED, "this launch shape does not fit shared memory");
+    const int oJ = P->fused_J, oaJ = P->adj_J, ont = P->fused_nT;
+    P->fused_J = J;
+    P->adj_J = adj_J;
+    P->fused_nT = nt;
+    const size_t vol = (size_t)g.nx * g.ny * g.nz, nproj = (size_t)g.nx * g.nz * g.nview;
+    const size_t per_view = std::max(vol, spect::fused_slab_per_view(*P));
+    const int chunk = (int)std::max<size_t>(
+        1, std::min<size_t>((size_t)g.nview, slab_budget_bytes(true) / (per_view * sizeof(float))));
+    spect_status r = realloc_floats(P, &P->slab, &P->slab_cap, per_view * (size_t)chunk, st, "work slab");
+    if (r == SPECT_OK)
+        r = realloc_floats(P, &P->part, &P->part_cap, nproj * (size_t)spect::fused_groups(*P), st,
+                           "depth-group partial sums");
+    if (r != SPECT_OK) {
+        P->fused_J = oJ;
+        P->adj_J = oaJ;
+        P->fused_nT = ont;
+        return r;
+    }
+    P->chunk = chunk;
+    P->adj_chunk = chunk;
+    return SPECT_OK;
+}
+
+// Device time of one call of fn (best of `reps` after one warm-up run).
+template <class F>
+spect_status time_best(cudaStream_t st, int reps, float* best, F&& fn)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        cudaGetLastError();
+        return fail(SPECT_ECUDA, "event creation failed");
+    }
+    spect_status r = fn();
+    *best = 1e30f;
+    for (int k = 0; k < reps && r == SPECT_OK; ++k) {
+        cudaEventRecord(a, st);
+        r = fn();
+        cudaEventRecord(b, st);
+        float ms = 0.f;
+        if (r == SPECT_OK && cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess)
+            *best = std::min(*best, ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaError_t e = cudaGetLastError();
+    if (r == SPECT_OK && e != cudaSuccess) r = fail(SPECT_ECUDA, std::string("timing: ") + cudaGetErrorString(e));
+    return r;
+}
+
+struct Tuned {
+    int J, adj_J, tiles;
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int, int, int>, Tuned> g_tuned;  // per geometry and device
+
+}  // namespace
+
+extern "C" {
+
+spect_status spect_plan_set_tuning(spect_plan P, int fused_J, int adj_J, int tiles, spect_stream stream)
+{
+    if (!P) return fail(SPECT_EINVAL, "plan is NULL");
+    return reconfigure(P, fused_J, adj_J, tiles, (cudaStream_t)stream);
+}
+
+spect_status spect_plan_get_tuning(spect_plan P, int* fused_J, int* adj_J, int* tiles)
+{
+    if (!P) return fail(SPECT_EINVAL, "plan is NULL");
+    if (fused_J) *fused_J = P->fused_J;
+    if (adj_J) *adj_J = P->adj_J;
+    if (tiles) *tiles = P->fused_nT;
+    return SPECT_OK;
+}
+
+spect_status spect_plan_autotune(spect_plan P, spect_stream stream)
+{
+    if (!P) return fail(SPECT_EINVAL, "plan is NULL");
+    if (!P->fast) return SPECT_OK;  // the low-memory kernels have no launch shape to choose
+    cudaStream_t st = (cudaStream_t)stream;
+    const Geometry& g = P->g;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, g.nx, g.nz, g.nview, g.nvp, P->bucket, (int)P->g.has_mu);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) return reconfigure(P, it->second.J, it->second.adj_J, it->second.tiles, st);
+    }
+    // inputs of the timed calls: the plan's own scratch (x_t = 1, v = 1)
+    const size_t vol = (size_t)g.nx * g.ny * g.nz, nproj = (size_t)g.nx * g.nz * g.nview;
+    if (spect::launch_fill(P->xt, vol, 1.f, st) != cudaSuccess ||
+        spect::launch_fill(P->ratio, nproj, 1.f, st) != cudaSuccess)
+        return fail(SPECT_ECUDA, "fill launch failed");
+    const int prof = P->prof;
+    P->prof = 0;
+    const int base = P->fused_nT;
+    const int nib = (g.nx + 15) / 16;
+    std::vector<int> tile_cands;
+    for (int t : {base, base + 1, 2 * base, 4 * base})
+        if (t <= nib && std::find(tile_cands.begin(), tile_cands.end(), t) == tile_cands.end()) tile_cands.push_back(t);
+    std::vector<int> Js;
+    for (int J : {4, 8, 16})
+        if (J <= std::max(g.ny, 4)) Js.push_back(J);
+    Tuned best{P->fused_J, P->adj_J, base};
+    float best_ms = 1e30f;
+    spect_status r = SPECT_OK;
+    for (int t : tile_cands) {
+        float fbest = 1e30f, abest = 1e30f;
+        int fJ = 0, aJ = 0;
+        for (int J : Js) {
+            if (reconfigure(P, J, Js.front(), t, st) != SPECT_OK) continue;
+            float ms = 0.f;
+            r = time_best(st, 3, &ms, [&] { return fast_forward(P, P->xt, P->ratio, nullptr, nullptr, st); });
+            if (r != SPECT_OK) break;
+            if (ms < fbest) fbest = ms, fJ = J;
+        }
+        if (r != SPECT_OK) break;
+        for (int J : Js) {
+            if (!fJ || reconfigure(P, fJ, J, t, st) != SPECT_OK) continue;
+            float ms = 0.f;
+            r = time_best(st, 3, &ms, [&] { return fast_back(P, P->ratio, P->et, spect::EmArgs(), st); });
+            if (r != SPECT_OK) break;
+            if (ms < abest) abest = ms, aJ = J;
+        }
+        if (r != SPECT_OK) break;
+        if (fJ && aJ && fbest + abest < best_ms) {
+            best_ms = fbest + abest;
+            best = {fJ, aJ, t};
+        }
+    }
+    P->prof = prof;
+    if (r != SPECT_OK) return r;
+    r = reconfigure(P, best.J, best.adj_J, best.tiles, st);
+    if (r != SPECT_OK) return r;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = best;
+    return SPECT_OK;
+}
+
+spect_status spect_batch_create(spect_batch* out, const spect_plan* plans, int n)
+{
+    if (!out) return fail(SPECT_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!plans || n < 1) return fail(SPECT_EINVAL, "need at least one plan");
+    for (int i = 0; i < n; ++i) {
+        if (!plans[i]) return fail(SPECT_EINVAL, "plan is NULL");
+        for (int k = 0; k < i; ++k)
+            if (plans[k] == plans[i]) return fail(SPECT_EINVAL, "a plan appears twice in the batch");
+    }
+    spect_batch_s* B = new spect_batch_s();
+    B->plans.assign(plans, plans + n);
+    const int ns = std::min(n, 32);
+    cudaError_t e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->origin, cudaStreamNonBlocking);
+    for (int i = 0; i < ns && e == cudaSuccess; ++i) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t j = nullptr;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) B->side.push_back(s);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+        if (e == cudaSuccess) B->join.push_back(j);
+    }
+    if (e != cudaSuccess) {
+        spect_batch_destroy(B);
+        cudaGetLastError();
+        return fail(SPECT_ECUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
+    }
+    *out = B;
+    return SPECT_OK;
+}
+
+spect_status spect_batch_em_step(spect_batch B, float* const* x, const float* const* y, const float* const* rbar,
+                                 int niter, spect_stream stream)
+{
+    if (!B) return fail(SPECT_EINVAL, "batch is NULL");
+    if (!x || !y) return fail(SPECT_EINVAL, "x and y pointer arrays are required");
+    if (niter < 0) return fail(SPECT_EINVAL, "niter must be >= 0");
+    const int n = (int)B->plans.size();
+    for (int i = 0; i < n; ++i) {
+        spect_status r = check_call(B->plans[i], x[i], y[i], "x", "y");
+        if (r != SPECT_OK) return r;
+        if (rbar && rbar[i] && !aligned16(rbar[i])) return fail(SPECT_EINVAL, "rbar is not 16-byte aligned");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    // sensitivities are computed outside the graph (once per plan)
+    for (spect_plan_s* P : B->plans) {
+        spect_status r = ensure_sensitivity(P, st);
+        if (r != SPECT_OK) return r;
+    }
+    if (niter == 0) return SPECT_OK;
+    std::vector<const void*> key;
+    key.push_back((const void*)(intptr_t)niter);
+    for (int i = 0; i < n; ++i) {
+        key.push_back(x[i]);
+        key.push_back(y[i]);
+        key.push_back(rbar ? rbar[i] : nullptr);
+    }
+    if (!B->exec || key != B->key) {
+        if (B->exec) cudaGraphExecDestroy(B->exec);
+        B->exec = nullptr;
+        std::vector<int> prof(n);
+        std::vector<long long> before(n);
+        for (int i = 0; i < n; ++i) {
+            prof[i] = B->plans[i]->prof;
+            B->plans[i]->prof = 0;  // no timing events inside the graph
+            before[i] = 0;
+            for (int k = 0; k < SPECT_K_COUNT; ++k) before[i] += B->plans[i]->launches[k];
+        }
+        // captured on the batch's own origin stream; launched on the caller's
+        cudaStream_t cs = B->origin;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        spect_status r = e == cudaSuccess ? SPECT_OK : fail(SPECT_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+        if (r == SPECT_OK) e = cudaEventRecord(B->fork, cs);
+        const int ns = (int)B->side.size();
+        for (int s = 0; s < ns && e == cudaSuccess; ++s) e = cudaStreamWaitEvent(B->side[s], B->fork, 0);
+        if (r == SPECT_OK && e != cudaSuccess) r = fail(SPECT_ECUDA, std::string("fork: ") + cudaGetErrorString(e));
+        for (int i = 0; i < n && r == SPECT_OK; ++i)
+            r = em_iterate(B->plans[i], x[i], y[i], rbar ? rbar[i] : nullptr, nullptr, 0.f, niter, B->side[i % ns]);
+        for (int s = 0; s < ns && r == SPECT_OK; ++s) {
+            e = cudaEventRecord(B->join[s], B->side[s]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, B->join[s], 0);
+            if (e != cudaSuccess) r = fail(SPECT_ECUDA, std::string("join: ") + cudaGetErrorString(e));
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);  // always ends the capture
+        if (r == SPECT_OK && e2 != cudaSuccess) r = fail(SPECT_ECUDA, std::string("end capture: ") + cudaGetErrorString(e2));
+        if (r == SPECT_OK) {
+            e = cudaGraphInstantiate(&B->exec, graph, 0);
+            if (e != cudaSuccess) {
+                B->exec = nullptr;
+                r = fail(SPECT_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+            }
+        }
+        if (graph) cudaGraphDestroy(graph);
+        long long total = 0;
+        for (int i = 0; i < n; ++i) {
+            B->plans[i]->prof = prof[i];
+            long long now = 0;
+            for (int k = 0; k < SPECT_K_COUNT; ++k) now += B->plans[i]->launches[k];
+            total += now - before[i];
+        }
+        cudaGetLastError();
+        if (r != SPECT_OK) return r;
+        B->graph_launches = total;
+        B->key = key;
+    }
+    cudaError_t e = cudaGraphLaunch(B->exec, st);
+    if (e != cudaSuccess) return fail(SPECT_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    return SPECT_OK;
+}
+
+spect_status spect_batch_info(spect_batch B, int* n_plans, long long* kernels_per_launch)
+{
+    if (!B) return fail(SPECT_EINVAL, "batch is NULL");
+    if (n_plans) *n_plans = (int)B->plans.size();
+    if (kernels_per_launch) *kernels_per_launch = B->graph_launches;
+    return SPECT_OK;
+}
+
+spect_status spect_batch_destroy(spect_batch B)
+{
+    if (!B) return SPECT_OK;
+    cudaError_t e = cudaSuccess;
+    for (cudaStream_t s : B->side) {
+        cudaError_t e1 = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = e1;
+    }
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    for (cudaStream_t s : B->side) cudaStreamDestroy(s);
+    if (B->origin) cudaStreamDestroy(B->origin);
+    for (cudaEvent_t j : B->join) cudaEventDestroy(j);
+    if (B->fork) cudaEventDestroy(B->fork);
+    delete B;
+    if (e != cudaSuccess) return fail(SPECT_ECUDA, std::string("batch destroy: ") + cudaGetErrorString(e));
     return SPECT_OK;
 }
 

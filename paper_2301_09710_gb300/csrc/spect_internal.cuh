@@ -67,6 +67,8 @@ struct spect_plan_s {
     int* adj_off = nullptr;      // nview*nx*ny + 1
     spect::AdjEntry* adj = nullptr;
     float* slab = nullptr;       // chunk * nx*ny*nz
+    size_t slab_cap = 0;         // floats allocated for slab
+    size_t part_cap = 0;         // floats allocated for part
     float* e = nullptr;          // nx*ny*nz  (EM back-projection accumulator)
     float* ratio = nullptr;      // nx*nz*nview (EM ratio / ones)
     float* s = nullptr;          // nx*ny*nz  (sensitivity A'1)
@@ -308,6 +310,7 @@ int choose_sep_tile(const Geometry& g, int cls_z, size_t smem_limit);
 // they do not fit; *tiles receives the column-tile count they need.
 int fused_bucket(const Geometry& g, size_t smem_limit, int* tiles);
 int fused_groups(const spect_plan_s& P);
+int fused_tiles_fit(const Geometry& g, int bucket, int J, int adj_J, int tiles, size_t smem_limit);
 cudaError_t launch_transpose(const float* in, float* out, int R, int C, cudaStream_t st);
 cudaError_t launch_mubar_cache(const spect_plan_s& P, const float* mu_t, cudaStream_t st);
 cudaError_t launch_build_adjacency_fixed(const spect_plan_s& P, cudaStream_t st);

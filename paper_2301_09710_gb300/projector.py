@@ -205,6 +205,23 @@ class SpectPlan:
         _lib.check(self.lib.spect_profile_read(self.handle, la, ms, int(bool(reset))))
         return {k: (la[i], ms[i]) for i, k in enumerate(_lib.KERNEL_CLASSES)}
 
+    # ------------------------------------------------------------------ launch shapes
+    @property
+    def tuning(self) -> dict:
+        """fused_J / adj_J: depth planes per forward / adjoint blur block; tiles: column tiles per plane."""
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _lib.check(self.lib.spect_plan_get_tuning(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"fused_J": a.value, "adj_J": b.value, "tiles": c.value}
+
+    def set_tuning(self, fused_J: int, adj_J: int, tiles: int, stream=None) -> None:
+        _lib.check(self.lib.spect_plan_set_tuning(self.handle, int(fused_J), int(adj_J), int(tiles),
+                                                  _stream_handle(stream)))
+
+    def autotune(self, stream=None) -> dict:
+        """Time the candidate launch shapes on this device and keep the fastest (cached per geometry)."""
+        _lib.check(self.lib.spect_plan_autotune(self.handle, _stream_handle(stream)))
+        return self.tuning
+
     def release(self, stream) -> None:
         """Free the plan after the work already enqueued on ``stream``, without
         waiting for the device (all of the plan's work must be on ``stream``)."""
@@ -228,3 +245,51 @@ class SpectPlan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class SpectBatch:
+    """Plans of different sizes whose EM iterations run as one CUDA graph launch
+    (one graph branch per plan; see spect_batch_em_step)."""
+
+    def __init__(self, plans):
+        self.lib = _lib.load()
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        handle = ctypes.c_void_p()
+        _lib.check(self.lib.spect_batch_create(ctypes.byref(handle), arr, len(self.plans)))
+        self.handle = handle
+
+    def em_step(self, xs, ys, rbars=None, niter: int = 1, stream=None):
+        """niter MLEM updates of every plan's x in place (xs, ys, rbars: lists of CUDA tensors)."""
+        n = len(self.plans)
+        if len(xs) != n or len(ys) != n or (rbars is not None and len(rbars) != n):
+            raise ValueError("one x, y (and rbar) per plan")
+        for p, x, y in zip(self.plans, xs, ys):
+            p._check(x, p.vol_shape, "x")
+            p._check(y, p.proj_shape, "y")
+        if rbars is not None:
+            for p, r in zip(self.plans, rbars):
+                if r is not None:
+                    p._check(r, p.proj_shape, "rbar")
+        P = ctypes.c_void_p * n
+        xa = P(*[x.data_ptr() for x in xs])
+        ya = P(*[y.data_ptr() for y in ys])
+        ra = P(*[(r.data_ptr() if r is not None else None) for r in rbars]) if rbars is not None else None
+        _lib.check(self.lib.spect_batch_em_step(self.handle, xa, ya, ra, int(niter), _stream_handle(stream)))
+        return xs
+
+    def info(self) -> dict:
+        n, k = ctypes.c_int(), ctypes.c_longlong()
+        _lib.check(self.lib.spect_batch_info(self.handle, ctypes.byref(n), ctypes.byref(k)))
+        return {"plans": n.value, "kernels_per_launch": k.value}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _lib.check(self.lib.spect_batch_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
