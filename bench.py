@@ -113,6 +113,7 @@ def make_workload(device, path, nview=NVIEW):
     sep = path == "separable"
     if sep:
         plan = SpectPlan(NX, NZ, nview, mu=prob.mu, dy=prob.dy, fx=prob.fx, fz=prob.fz, device=device)
+        plan.autotune()  # the library's launch-shape autotuner (timed on this device, outside the timed region)
     else:
         plan = SpectPlan(NX, NZ, nview, mu=prob.mu, dy=prob.dy, psf=prob.full_psf(), device=device)
     xt = torch.from_numpy(prob.x).to(device)
@@ -295,6 +296,7 @@ def run_ours(args):
                                       "anisotropic Gaussian PSF (separable factors), MLEM step with 10% smoothed "
                                       "background, XCAT-like ellipsoid phantom (seed 0)",
                           "path": args.path, "fused": info["fused"], "view_chunk": chunk, "nview": args.nview, "parallelism": f"replicas{world}",
+                          "launch_shape": plan.tuning if info["fused"] else None,
                           "l2": "flushed between timed steps (256 MB write)",
                           "step": "one EM iteration = one A + one A' + fused ratio/update"},
                "clocks": clk.summary(), "gpu_launches": n_launch, "e2e": e2e, "roofline": roofline,

@@ -317,15 +317,20 @@ __device__ __forceinline__ void flag_timeout(int* err)
 
 constexpr int kRotThreads = 512;
 
-template <int P>
+// MUS: the plane's attenuation factors arrive by one TMA bulk load into shared
+// memory (issued first, waited for after the first gathers are in flight)
+// instead of as per-element global loads, when the two planes fit.
+template <int P, bool MUS>
 __global__ void __launch_bounds__(kRotThreads, 2) k_rot_fwd(Geometry g, FusedDims d, const float* __restrict__ rtab,
                                                          const float* __restrict__ xt,
                                                          const float* __restrict__ mubar, float* __restrict__ wsl,
-                                                         int l0)
+                                                         int l0, int* err)
 {
     constexpr int C = Sep<P>::C;
     extern __shared__ __align__(16) float sm[];
     float* S = sm;
+    float* MU = sm + d.farea;  // [i][k] attenuation plane (MUS)
+    uint64_t* bar = reinterpret_cast<uint64_t*>(MU + d.ps);
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = kRotThreads / 32;
@@ -337,6 +342,15 @@ __global__ void __launch_bounds__(kRotThreads, 2) k_rot_fwd(Geometry g, FusedDim
     const float4* TW = reinterpret_cast<const float4*>(tab);
     const int* TB = reinterpret_cast<const int*>(tab + 4 * nx);
     const float* mb = mubar + ((size_t)l * ny + j) * d.ps;
+    if (MUS) {
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            tma_load_1d(MU, mb, (unsigned)d.ps * 4u, bar);
+        }
+        __syncthreads();  // the barrier is initialised before anyone waits on it
+    }
+    bool ok = true, waited = !MUS;
 
     for (int i = 2 * warp; i < nx; i += 2 * NW) {
         const bool two = i + 1 < nx;
@@ -358,14 +372,24 @@ __global__ void __launch_bounds__(kRotThreads, 2) k_rot_fwd(Geometry g, FusedDim
                     xb[q][1] = __ldg(pb + nz + k);
                     xb[q][2] = __ldg(pb + pln + k);
                     xb[q][3] = __ldg(pb + pln + nz + k);
-                    ma[q] = __ldg(mb + i * nz + k);
-                    mc[q] = two ? __ldg(mb + (i + 1) * nz + k) : 0.f;
+                    if (!MUS) {
+                        ma[q] = __ldg(mb + i * nz + k);
+                        mc[q] = two ? __ldg(mb + (i + 1) * nz + k) : 0.f;
+                    }
                 }
+            }
+            if (!waited) {
+                ok = mbar_wait_bounded(bar, 0u);
+                waited = true;
             }
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const int k = k0 + 32 * q + lane;
                 if (k < nz) {
+                    if (MUS) {
+                        ma[q] = MU[i * nz + k];
+                        mc[q] = two ? MU[(i + 1) * nz + k] : 0.f;
+                    }
                     float* wr = S + k * wp + C;
                     float va = wa.x * xa[q][0];
                     va = fmaf(wa.y, xa[q][1], va);
@@ -391,7 +415,13 @@ __global__ void __launch_bounds__(kRotThreads, 2) k_rot_fwd(Geometry g, FusedDim
             }
         }
     }
-    __syncthreads();
+    if (__syncthreads_or(!ok)) {  // the attenuation plane never arrived
+        if (threadIdx.x == 0) {
+            flag_timeout(err);
+            mbar_wait_bounded(bar, 0u);  // a last chance for the copy in flight to land
+        }
+        return;
+    }
     float* dst = wsl + ((size_t)v * ny + j) * d.parea;
     if (d.nT == 1) {
         if (threadIdx.x == 0) {
@@ -958,10 +988,13 @@ template <int P>
 cudaError_t rot_launch(const spect_plan_s& Pl, const float* xt, int l0, int nv, cudaStream_t st)
 {
     const FusedDims d = dims_for<P>(Pl.g, Pl.fused_J, Pl.fused_nT);
-    const size_t smem = (size_t)d.farea * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_rot_fwd<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem_mu = ((size_t)d.farea + d.ps) * sizeof(float) + 16;
+    const bool mus = smem_mu <= (size_t)Pl.smem_optin;
+    const size_t smem = mus ? smem_mu : (size_t)d.farea * sizeof(float);
+    auto kern = mus ? k_rot_fwd<P, true> : k_rot_fwd<P, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_rot_fwd<P><<<dim3(Pl.g.ny, nv), kRotThreads, smem, st>>>(Pl.g, d, Pl.rtab, xt, Pl.mubar, Pl.slab, l0);
+    kern<<<dim3(Pl.g.ny, nv), kRotThreads, smem, st>>>(Pl.g, d, Pl.rtab, xt, Pl.mubar, Pl.slab, l0, Pl.err);
     return cudaGetLastError();
 }
 

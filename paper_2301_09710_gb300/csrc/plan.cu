@@ -456,6 +456,7 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
 
     PLAN_TRY(cudaGetDevice(&dev), "cudaGetDevice");
     PLAN_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "device query");
+    P->smem_optin = smem_optin;
     {
         int pools = 0;
         PLAN_TRY(cudaDeviceGetAttribute(&pools, cudaDevAttrMemoryPoolsSupported, dev), "device query");
@@ -578,6 +579,7 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
     P->adj_J = 8;
     if (const char* env = getenv("SPECT_ADJ_CHUNK")) {
         if (atoi(env) > 0) {
+            P->adj_chunk_req = atoi(env);
             P->adj_chunk = std::min(std::min(atoi(env), nview), P->chunk);
             int sms = 0;
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -875,7 +877,7 @@ spect_status reconfigure(spect_plan_s* P, int J, int adj_J, int tiles, cudaStrea
         return r;
     }
     P->chunk = chunk;
-    P->adj_chunk = chunk;
+    P->adj_chunk = P->adj_chunk_req > 0 ? std::min(P->adj_chunk_req, chunk) : chunk;
     return SPECT_OK;
 }
 

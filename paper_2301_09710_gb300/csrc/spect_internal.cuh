@@ -78,12 +78,14 @@ struct spect_plan_s {
     // fast path (fused kernels, k-fastest internal layout, cached attenuation)
     cudaStream_t home = nullptr; // creation stream (stream-ordered allocations)
     bool pooled = false;         // memory from cudaMallocAsync (freed with cudaFreeAsync)
+    int smem_optin = 0;          // shared memory a block may opt in to (bytes)
     int fast = 0;                // 1 when the fused kernels serve this plan
     int bucket = 0;              // padded tap count of the fused kernels
     int fused_J = 8;             // depth planes per fused forward block
     int fused_nT = 1;            // column tiles per plane in the fused kernels
     int adj_J = 8;               // depth planes per fused adjoint block
     int adj_chunk = 0;           // views per adjoint pass (t slab sized to stay in L2)
+    int adj_chunk_req = 0;       // views per adjoint pass asked for (SPECT_ADJ_CHUNK), 0: all
     float* mubar = nullptr;      // nview * ny*nx*nz, [l][j][i][k]
     float* xt = nullptr;         // nx*ny*nz, [j][i][k] image
     float* et = nullptr;         // nx*ny*nz, [j][i][k] back-projection accumulator
