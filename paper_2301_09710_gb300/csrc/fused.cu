@@ -250,9 +250,10 @@ struct FusedDims {
 
 __host__ __device__ inline size_t fwd_smem_floats(const FusedDims& d, int nz, int PT)
 {
-    // W x2 | U | taps J x (FX,FZ) | ACC | folded edge taps J x 2 x nz | 2 mbarriers
+    // W x2 | U | taps J x (FX,FZ) | ACC | folded edge taps J x 2 x (nkb*16) | 2 mbarriers
+    (void)nz;
     return 2 * (size_t)d.warea + (size_t)d.urows * d.kpu + 2 * (size_t)PT * d.J + (size_t)d.urows * d.apc +
-           2 * (size_t)d.J * nz + 10;
+           2 * (size_t)d.J * d.nkb * 16 + 8;
 }
 
 __host__ __device__ inline size_t adj_smem_floats(const FusedDims& d, int PT)
@@ -464,8 +465,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
     float* U = WB + 2 * (size_t)d.warea;
     float* TAP = U + (size_t)d.urows * d.kpu;          // [J][FX PT | FZ PT], every plane of the group
     float* ACC = TAP + 2 * PT * (size_t)d.J;           // urows x apc, [i - i0][k]
-    float* FOLD = ACC + (size_t)d.urows * d.apc;        // [J][2][nz] folded edge taps of the k-pass
-    uint64_t* bar = reinterpret_cast<uint64_t*>(FOLD + ((2 * (size_t)d.J * nz + 1) & ~(size_t)1));
+    const int fs = d.nkb * CZ;                          // folded-tap row length (zero beyond nz)
+    float* FOLD = ACC + (size_t)d.urows * d.apc;        // [J][2][fs] folded edge taps of the k-pass
+    uint64_t* bar = reinterpret_cast<uint64_t*>(FOLD + 2 * (size_t)d.J * fs);
     const int tid = threadIdx.x;
     constexpr int T = kFusedThreads;
     const int grp = blockIdx.x, v = blockIdx.y, l = l0 + v;
@@ -500,30 +502,35 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
     __syncthreads();
     // replicate padding along k, folded: output k takes U(0) * sum_{b > k+C} fz(b)
     // and U(nz-1) * sum_{b < k+C-nz+1} fz(b) on top of the zero-padded k-pass
-    for (int e = tid; e < (j_end - j_begin) * nz; e += T) {
-        const int jj = e / nz, k = e - jj * nz;
+    for (int e = tid; e < (j_end - j_begin) * fs; e += T) {
+        const int jj = e / fs, k = e - jj * fs;
         const float* f = TAP + jj * 2 * PT + PT;
         float lo = 0.f, hi = 0.f;
-        for (int bq = k + C + 1; bq < P; ++bq) lo += f[bq];
-        for (int bq = 0; bq < k + C - nz + 1 && bq < P; ++bq) hi += f[bq];
-        FOLD[(jj * 2) * nz + k] = lo;
-        FOLD[(jj * 2 + 1) * nz + k] = hi;
+        if (k < nz) {
+            for (int bq = k + C + 1; bq < P; ++bq) lo += f[bq];
+            for (int bq = 0; bq < k + C - nz + 1 && bq < P; ++bq) hi += f[bq];
+        }
+        FOLD[(jj * 2) * fs + k] = lo;
+        FOLD[(jj * 2 + 1) * fs + k] = hi;
     }
     __syncthreads();
 
-    unsigned phase[2] = {0u, 0u};
+    // the thread's first work item of each pass (the same for every plane)
+    const int ip_ib = tid / nz, ip_k = tid - ip_ib * nz;    // i-pass: (column run, k)
+    const int kp_kb = tid / ti, kp_i = tid - kp_kb * ti;    // k-pass: (k run, column)
+    unsigned phases = 0u;                                   // bit b: parity of buffer b's barrier
     for (int j = j_begin; j < j_end; ++j) {
         const int b = (j - j_begin) & 1;
         const float* FX = TAP + (j - j_begin) * 2 * PT;
         const float* FZ = FX + PT;
         const float* W = WB + b * (size_t)d.warea;
-        const bool ok = mbar_wait_bounded(bar + b, phase[b]);
-        phase[b] ^= 1u;
+        const bool ok = mbar_wait_bounded(bar + b, (phases >> b) & 1u);
+        phases ^= 1u << b;
 
         // i-pass: U(i,k) = sum_a fx(a) w(clamp(i-a+cx), k); lanes over k
         if (ok) {
+            int ib = ip_ib, k = ip_k;
             for (int it = tid; it < nz * nibt; it += T) {
-                const int ib = it / nz, k = it - ib * nz;
                 const int li = ib * CX;  // first column of this run, relative to the tile
                 const float* wr = W + k * d.wp + li;
                 float win[CX + P - 1];
@@ -540,13 +547,16 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
                     for (int c = 0; c < CX; ++c)
                         if (li + c < ti) ur[c * d.kpu] = o[c];
                 }
+                ib += T / nz;  // next item: it + T
+                k += T % nz;
+                if (k >= nz) k -= nz, ++ib;
             }
         }
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 flag_timeout(err);
-                mbar_wait_bounded(bar + b, phase[b] ^ 1u);  // give the copies in flight a last chance to land
-                mbar_wait_bounded(bar + (b ^ 1), phase[b ^ 1]);
+                mbar_wait_bounded(bar + b, ((phases >> b) & 1u) ^ 1u);  // a last chance for the copies in flight
+                mbar_wait_bounded(bar + (b ^ 1), (phases >> (b ^ 1)) & 1u);
             }
             return;
         }
@@ -559,22 +569,39 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
 
         // k-pass into the depth-sum accumulators: lanes over i; zero-padded
         // FIR plus the folded replicate-padding terms on the edge rows
-        const float* fold_lo = FOLD + (j - j_begin) * 2 * nz;
-        const float* fold_hi = fold_lo + nz;
+        const float* fold_lo = FOLD + (j - j_begin) * 2 * fs;
+        const float* fold_hi = fold_lo + fs;
+        int kb = kp_kb, i = kp_i;  // i relative to the tile
         for (int it = tid; it < ti * d.nkb; it += T) {
-            const int kb = it / ti, i = it - kb * ti;  // i relative to the tile
             const float* ur = U + i * d.kpu;
             float win[WZ];
             load_window_f4<P>(ur + kb * CZ, win);
             float o[CZ];
             fir<P, CZ, -1, C + ZH>(FZ, win, o);
             const int k0 = kb * CZ;
-            if (k0 < C || k0 + CZ > nz - C) {
-                const float ulo = ur[ZH], uhi = ur[ZH + nz - 1];
+            // folded taps are zero outside the first and last C rows
+            if (k0 + CZ > nz - C) {
+                const float uhi = ur[ZH + nz - 1];
+                const float4* f4 = reinterpret_cast<const float4*>(fold_hi + k0);
 #pragma unroll
-                for (int c = 0; c < CZ; ++c) {
-                    const int k = min(k0 + c, nz - 1);
-                    o[c] = fmaf(ulo, fold_lo[k], fmaf(uhi, fold_hi[k], o[c]));
+                for (int c4 = 0; c4 < CZ / 4; ++c4) {
+                    const float4 f = f4[c4];
+                    o[4 * c4] = fmaf(uhi, f.x, o[4 * c4]);
+                    o[4 * c4 + 1] = fmaf(uhi, f.y, o[4 * c4 + 1]);
+                    o[4 * c4 + 2] = fmaf(uhi, f.z, o[4 * c4 + 2]);
+                    o[4 * c4 + 3] = fmaf(uhi, f.w, o[4 * c4 + 3]);
+                }
+            }
+            if (k0 < C) {
+                const float ulo = ur[ZH];
+                const float4* f4 = reinterpret_cast<const float4*>(fold_lo + k0);
+#pragma unroll
+                for (int c4 = 0; c4 < CZ / 4; ++c4) {
+                    const float4 f = f4[c4];
+                    o[4 * c4] = fmaf(ulo, f.x, o[4 * c4]);
+                    o[4 * c4 + 1] = fmaf(ulo, f.y, o[4 * c4 + 1]);
+                    o[4 * c4 + 2] = fmaf(ulo, f.z, o[4 * c4 + 2]);
+                    o[4 * c4 + 3] = fmaf(ulo, f.w, o[4 * c4 + 3]);
                 }
             }
             float4* acc4 = reinterpret_cast<float4*>(ACC + i * d.apc + kb * CZ);
@@ -587,6 +614,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
                 a.w += o[4 * c4 + 3];
                 acc4[c4] = a;
             }
+            kb += T / ti;  // next item: it + T
+            i += T % ti;
+            if (i >= ti) i -= ti, ++kb;
         }
         __syncthreads();
     }
