@@ -1,0 +1,332 @@
+// gather.cu -- adjoint rotation and view sum of A' (Section II-A, Algorithm 2)
+// as a patch-staged gather:
+//
+//   x_t(q, k) = sum_l sum_{(p, w) in adj(l, q)} w * t_l(p, k)
+//
+// One block owns an 8x8 patch of destination columns q and a run of KC
+// consecutive k.  For every view, the source pixels its destinations read lie
+// in a small box of the rotated frame (at most about 8*sqrt(2) + 2 on a side);
+// the box is brought into shared memory by one TMA tensor load (3D tile of the
+// t slab: k x i x plane) and the patch's adjacency entries by one bulk copy,
+// several views ahead of use, so the gathers read shared memory instead of
+// waiting on L2.  The entries hold box-local offsets computed at plan time from
+// the fixed-length lists k_build_adjacency_fixed writes (same weights, same
+// order), and the per-view sum and the Kahan sum over views are those of
+// k_adj_rot_t: the results are bitwise the same.
+#include <cuda.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdlib>
+#include <vector>
+
+#include "spect_internal.cuh"
+
+namespace spect {
+
+namespace {
+
+constexpr int kGT = 256;      // threads: 64 destinations x 4 float4 groups of k
+constexpr int kPatch = 8;     // destinations per patch side
+constexpr int kStages = 4;    // views in flight per block
+
+// Box of source pixels read by patch `patch` in view l: (i0, j0, width, height).
+__global__ void k_patch_boxes(Geometry g, int ps, int maxe, const AdjEntry* __restrict__ adjf, int npx, int4* boxes)
+{
+    __shared__ int mn_i, mn_j, mx_i, mx_j;
+    const int patch = blockIdx.x, l = blockIdx.y, t = threadIdx.x;
+    if (t == 0) {
+        mn_i = mn_j = INT_MAX;
+        mx_i = mx_j = INT_MIN;
+    }
+    __syncthreads();
+    const int qi = (patch % npx) * kPatch + (t % kPatch), qj = (patch / npx) * kPatch + (t / kPatch);
+    if (qi < g.nx && qj < g.ny) {
+        const AdjEntry* e = adjf + ((size_t)(qj * g.nx + qi) * g.nview + l) * maxe;
+        for (int m = 0; m < maxe; ++m) {
+            if (e[m].w == 0.f) continue;
+            const int pj = e[m].p / ps, pi = (e[m].p - pj * ps) / g.nz;
+            atomicMin(&mn_i, pi);
+            atomicMin(&mn_j, pj);
+            atomicMax(&mx_i, pi);
+            atomicMax(&mx_j, pj);
+        }
+    }
+    __syncthreads();
+    if (t == 0) {
+        int4 b = make_int4(0, 0, 0, 0);
+        if (mx_i >= mn_i) b = make_int4(mn_i, mn_j, mx_i - mn_i + 1, mx_j - mn_j + 1);
+        boxes[(size_t)patch * g.nview + l] = b;
+    }
+}
+
+// Patch entries [patch][l][64][maxe]: (box-local offset (row*BW + col)*KC, weight);
+// zero entries for padding and for destinations outside the image.
+__global__ void k_patch_entries(Geometry g, int ps, int maxe, const AdjEntry* __restrict__ adjf, int npx,
+                                const int4* __restrict__ boxes, int bw, int kc, AdjEntry* pent)
+{
+    const int patch = blockIdx.x, l = blockIdx.y, t = threadIdx.x;
+    const int qi = (patch % npx) * kPatch + (t % kPatch), qj = (patch / npx) * kPatch + (t / kPatch);
+    const int4 b = boxes[(size_t)patch * g.nview + l];
+    AdjEntry* out = pent + (((size_t)patch * g.nview + l) * (kPatch * kPatch) + t) * maxe;
+    const bool inside = qi < g.nx && qj < g.ny;
+    const AdjEntry* e = adjf + ((size_t)(qj * g.nx + qi) * g.nview + l) * maxe;
+    for (int m = 0; m < maxe; ++m) {
+        AdjEntry o;  // padding and outside destinations: weight 0 on the box's first element
+        o.p = 0;
+        o.w = 0.f;
+        if (inside && e[m].w != 0.f) {
+            const int pj = e[m].p / ps, pi = (e[m].p - pj * ps) / g.nz;
+            o.p = ((pj - b.y) * bw + (pi - b.x)) * kc;
+            o.w = e[m].w;
+        }
+        out[m] = o;
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst_smem, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst_smem)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+struct GatherArgs {
+    Geometry g;
+    int npx;         // patches along i
+    int bw, bh, kc;  // box extents (the tensor map's box: kc x bw x bh)
+    int box_floats;  // bw * bh * kc
+    int ent_bytes;   // 64 * maxe * 8
+    int stage_floats;
+    int l0, nv;      // views [l0, l0 + nv) of the plan; slab view v holds view l0 + v
+};
+
+template <int MAXE>
+__global__ void __launch_bounds__(kGT) k_adj_gather(const __grid_constant__ CUtensorMap tmap, GatherArgs a,
+                                                    const int4* __restrict__ boxes, const AdjEntry* __restrict__ pent,
+                                                    float* out, int accumulate, EmArgs em, int* err)
+{
+    extern __shared__ __align__(128) float sm[];
+    const Geometry& g = a.g;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + (size_t)kStages * a.stage_floats);
+    const int patch = blockIdx.x, kc0 = blockIdx.y * a.kc;
+    const int tid = threadIdx.x;
+    const int ql = tid >> 2, k4 = tid & 3;  // destination in the patch, float4 group of k
+    const int qi = (patch % a.npx) * kPatch + (ql % kPatch), qj = (patch / a.npx) * kPatch + (ql / kPatch);
+
+    auto issue = [&](int v) {  // views in flight: stage v % kStages
+        const int s = v % kStages;
+        float* st = sm + (size_t)s * a.stage_floats;
+        const int l = a.l0 + v;
+        const int4 b = boxes[(size_t)patch * g.nview + l];
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar + s)),
+                     "r"((unsigned)(a.box_floats * 4 + a.ent_bytes))
+                     : "memory");
+        tma_load_3d(st, &tmap, kc0, b.x, v * g.ny + b.y, bar + s);
+        tma_copy_1d(st + a.box_floats, pent + ((size_t)patch * g.nview + l) * (kPatch * kPatch) * MAXE,
+                    (unsigned)a.ent_bytes, bar + s);
+    };
+    // tensor copies want 128-byte aligned shared memory: refuse (error word) rather than fault
+    if ((smem_u32(sm) & 127u) != 0) {
+        if (tid == 0 && err) atomicExch(err, (int)SPECT_ECUDA);
+        return;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(bar + s, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int v = 0; v < kStages && v < a.nv; ++v) issue(v);
+    }
+    __syncthreads();
+
+    KSum acc[4];
+    for (int v = 0; v < a.nv; ++v) {
+        const int s = v % kStages;
+        const bool ok = mbar_wait_bounded(bar + s, (unsigned)(v / kStages) & 1u);
+        if (ok) {
+            const float* box = sm + (size_t)s * a.stage_floats;
+            const AdjEntry* e = reinterpret_cast<const AdjEntry*>(box + a.box_floats) + ql * MAXE;
+            AdjEntry en[MAXE];
+#pragma unroll
+            for (int m = 0; m < MAXE; ++m) en[m] = e[m];
+            float4 tv[MAXE];
+#pragma unroll
+            for (int m = 0; m < MAXE; ++m) tv[m] = *reinterpret_cast<const float4*>(box + en[m].p + 4 * k4);
+            float sv[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int m = 0; m < MAXE; ++m) {
+                sv[0] = fmaf(en[m].w, tv[m].x, sv[0]);
+                sv[1] = fmaf(en[m].w, tv[m].y, sv[1]);
+                sv[2] = fmaf(en[m].w, tv[m].z, sv[2]);
+                sv[3] = fmaf(en[m].w, tv[m].w, sv[3]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u].add(sv[u]);
+        }
+        if (__syncthreads_or(!ok)) {  // a copy never landed: give the ones in flight a last chance, then stop
+            if (tid == 0) {
+                if (err) atomicExch(err, (int)SPECT_ETIMEOUT);
+                for (int u = v; u < v + kStages && u < a.nv; ++u)
+                    mbar_wait_bounded(bar + (u % kStages), (unsigned)(u / kStages) & 1u);
+            }
+            return;
+        }
+            if (tid == 0 && v + kStages < a.nv) {  // stage s has been read by every thread
+            fence_proxy_async_smem();
+            issue(v + kStages);
+        }
+    }
+
+    const int k = kc0 + 4 * k4;
+    if (qi >= g.nx || qj >= g.ny || k >= g.nz) return;
+    const size_t o = (size_t)(qj * g.nx + qi) * g.nz + k;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        float val = acc[u].value();
+        if (accumulate) val += out[o + u];
+        if (em.x) em.x[o + u] = em_update(em.x[o + u], val, em.s[o + u], em.u ? em.u[o + u] : 0.f, em.beta);
+        else out[o + u] = val;
+    }
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn()
+{
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// floats per pipeline stage: the box, then the entries, rounded up to 128 bytes
+int stage_floats(int box_floats, int ent_bytes) { return (box_floats + ent_bytes / 4 + 31) & ~31; }
+
+size_t gather_smem(int box_floats, int ent_bytes)
+{
+    return (size_t)kStages * stage_floats(box_floats, ent_bytes) * sizeof(float) + kStages * sizeof(uint64_t);
+}
+
+}  // namespace
+
+int gather_kc() { return 16; }
+
+// Plan time: boxes, box extents and patch entries.  Leaves P.gather = 0 when
+// the geometry does not suit the kernel (k rows not a whole number of 16-byte
+// units, boxes too large for the tensor map or shared memory, no encoder).
+cudaError_t build_gather(spect_plan_s& P, cudaStream_t st)
+{
+    P.gather = 0;
+    const Geometry& g = P.g;
+    if (!P.fast || (g.nz % 4) != 0 || !encode_fn()) return cudaSuccess;
+    const char* env = getenv("SPECT_GATHER");  // 0: use the list gather k_adj_rot_t (testing)
+    if (env && atoi(env) == 0) return cudaSuccess;
+    const int npx = (g.nx + kPatch - 1) / kPatch, npy = (g.ny + kPatch - 1) / kPatch;
+    const size_t nb = (size_t)npx * npy * g.nview;
+    int4* boxes = nullptr;
+    cudaError_t e = P.pooled ? cudaMallocAsync((void**)&boxes, nb * sizeof(int4), st)
+                             : cudaMalloc((void**)&boxes, nb * sizeof(int4));
+    if (e != cudaSuccess) return e;
+    k_patch_boxes<<<dim3(npx * npy, g.nview), kPatch * kPatch, 0, st>>>(g, P.ps, P.adj_max, P.adjf, npx, boxes);
+    e = cudaGetLastError();
+    std::vector<int4> hb(nb);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), boxes, nb * sizeof(int4), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        if (P.pooled) cudaFreeAsync(boxes, st);
+        else cudaFree(boxes);
+        return e;
+    }
+    int bw = 1, bh = 1;
+    for (const int4& b : hb) {
+        bw = std::max(bw, b.z);
+        bh = std::max(bh, b.w);
+    }
+    const int kc = gather_kc();
+    const int box_floats = bw * bh * kc;
+    const int ent_bytes = kPatch * kPatch * P.adj_max * (int)sizeof(AdjEntry);
+    if (bw > 256 || bh > 256 || gather_smem(box_floats, ent_bytes) > (size_t)P.smem_optin ||
+        (size_t)box_floats * 4 + ent_bytes >= (1u << 20)) {
+        if (P.pooled) cudaFreeAsync(boxes, st);
+        else cudaFree(boxes);
+        return cudaSuccess;
+    }
+    const size_t nent = nb * kPatch * kPatch * P.adj_max;
+    AdjEntry* pent = nullptr;
+    e = P.pooled ? cudaMallocAsync((void**)&pent, nent * sizeof(AdjEntry), st)
+                 : cudaMalloc((void**)&pent, nent * sizeof(AdjEntry));
+    if (e != cudaSuccess) {
+        if (P.pooled) cudaFreeAsync(boxes, st);
+        else cudaFree(boxes);
+        return e;
+    }
+    k_patch_entries<<<dim3(npx * npy, g.nview), kPatch * kPatch, 0, st>>>(g, P.ps, P.adj_max, P.adjf, npx, boxes,
+                                                                         bw, kc, pent);
+    e = cudaGetLastError();
+    P.gboxes = boxes;
+    P.gent = pent;
+    P.bytes += nb * sizeof(int4) + nent * sizeof(AdjEntry);
+    P.gbw = bw;
+    P.gbh = bh;
+    P.gnpx = npx;
+    P.gnpy = npy;
+    P.gather = e == cudaSuccess;
+    return e;
+}
+
+cudaError_t launch_adj_gather(const spect_plan_s& P, int l0, int nv, float* out, int accumulate, EmArgs em,
+                              cudaStream_t st)
+{
+    const Geometry& g = P.g;
+    const int kc = gather_kc();
+    // the t slab as a 3D tensor: k (nz, contiguous) x i (nx, stride nz) x plane (chunk * ny, stride ps)
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.nz, (cuuint64_t)g.nx, (cuuint64_t)P.chunk * g.ny};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.nz * 4, (cuuint64_t)P.ps * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)kc, (cuuint32_t)P.gbw, (cuuint32_t)P.gbh};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, P.slab, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    GatherArgs a;
+    a.g = g;
+    a.npx = P.gnpx;
+    a.bw = P.gbw;
+    a.bh = P.gbh;
+    a.kc = kc;
+    a.box_floats = P.gbw * P.gbh * kc;
+    a.ent_bytes = kPatch * kPatch * P.adj_max * (int)sizeof(AdjEntry);
+    a.stage_floats = stage_floats(a.box_floats, a.ent_bytes);
+    a.l0 = l0;
+    a.nv = nv;
+    const size_t smem = gather_smem(a.box_floats, a.ent_bytes);
+    const dim3 grid(P.gnpx * P.gnpy, (g.nz + kc - 1) / kc);
+    switch (P.adj_max) {
+#define SPECT_G(M)                                                                                           \
+    case M: {                                                                                                \
+        cudaError_t e = cudaFuncSetAttribute(k_adj_gather<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                             (int)smem);                                                     \
+        if (e != cudaSuccess) return e;                                                                      \
+        k_adj_gather<M><<<grid, kGT, smem, st>>>(map, a, P.gboxes, P.gent, out, accumulate, em, P.err);      \
+        break;                                                                                               \
+    }
+        SPECT_G(1) SPECT_G(2) SPECT_G(3) SPECT_G(4) SPECT_G(5) SPECT_G(6) SPECT_G(7) SPECT_G(8)
+#undef SPECT_G
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace spect

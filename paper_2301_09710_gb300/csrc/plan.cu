@@ -133,7 +133,8 @@ void free_plan(spect_plan_s* P, cudaStream_t st)
     }
     for (cudaEvent_t e : P->evpool) cudaEventDestroy(e);
     void* ptrs[] = {P->mu, P->psf, P->psf_adj, P->fx, P->fz, P->fx_adj, P->fz_adj, P->rot, P->adj_off, P->adj,
-                    P->slab, P->e, P->ratio, P->s, P->mubar, P->xt, P->et, P->st, P->part, P->adjf, P->err, P->rtab, P->ut};
+                    P->slab, P->e, P->ratio, P->s, P->mubar, P->xt, P->et, P->st, P->part, P->adjf, P->err, P->rtab, P->ut,
+                    P->gboxes, P->gent};
     for (void* p : ptrs) raw_free(P, p, st);
     delete P;
 }
@@ -276,7 +277,10 @@ spect_status fast_back(spect_plan_s* P, const float* v, float* out_t, spect::EmA
         spect::EmArgs e = em;
         if (!last) e.x = nullptr;
         SPECT_CUDA_TRY(counted(P, SPECT_K_ROTATE_ADJ, st,
-                               [&] { return spect::launch_adj_rot_t(*P, l0, nv, out_t, l0 > 0, e, st); }),
+                               [&] {
+                                   return P->gather ? spect::launch_adj_gather(*P, l0, nv, out_t, l0 > 0, e, st)
+                                                    : spect::launch_adj_rot_t(*P, l0, nv, out_t, l0 > 0, e, st);
+                               }),
                        "adjoint rotation launch");
     }
     return SPECT_OK;
@@ -352,6 +356,9 @@ size_t plan_bytes_bound(const spect_plan_s& P)
     if (P.fast) {
         b += (size_t)g.ny * P.ps * g.nview * F + 4 * vol * F;
         b += nproj * (size_t)spect::fused_groups(P) * F + (size_t)g.nview * g.ny * P.ts * F;
+        // patch gather: boxes and box-local entries (at most 8 per list)
+        const size_t np = (size_t)((g.nx + 7) / 8) * ((g.ny + 7) / 8) * g.nview;
+        b += np * 16 + np * 64 * 8 * sizeof(spect::AdjEntry);
     }
     return b;
 }
@@ -605,6 +612,7 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
         PLAN_TRY(spect::launch_mubar_cache(*P, P->slab, st), "attenuation cache launch");
         PLAN_ALLOC(P->rtab, (size_t)nview * ny * P->ts, "rotation tables");
         PLAN_TRY(spect::launch_rot_tables(*P, st), "rotation table launch");
+        PLAN_TRY(spect::build_gather(*P, st), "patch gather set-up");
     }
     PLAN_TRY(cudaStreamSynchronize(st), "plan set-up");
     *out = P;

@@ -93,6 +93,11 @@ struct spect_plan_s {
     float* ut = nullptr;         // nx*ny*nz, [j][i][k] regulariser target of the regularised EM
     float* part = nullptr;       // G * nx*nz*nview forward partial sums
     spect::AdjEntry* adjf = nullptr;  // nview*nx*ny*adj_max fixed-length lists
+    // patch-staged adjoint gather (gather.cu); gather == 0: the list gather k_adj_rot_t
+    int gather = 0;
+    int4* gboxes = nullptr;      // [patch][l] source box (i0, j0, width, height)
+    spect::AdjEntry* gent = nullptr;  // [patch][l][64][adj_max] box-local entries
+    int gbw = 0, gbh = 0, gnpx = 0, gnpy = 0;
     int ps = 0;                  // plane stride of the attenuation cache and slab: nx*nz rounded up to 4
     int ts = 0;                  // rotation table block per (view, row): 5*nx rounded up to 4
     float* rtab = nullptr;       // nview*ny*ts rotation tables of the fused forward
@@ -322,6 +327,9 @@ cudaError_t launch_fused_rotate(const spect_plan_s& P, const float* xt, int l0, 
 size_t fused_slab_per_view(const spect_plan_s& P);
 cudaError_t launch_fused_adjoint(const spect_plan_s& P, const float* v, int l0, int nv, cudaStream_t st);
 cudaError_t launch_fwd_reduce(const spect_plan_s& P, float* v, const float* em_y, const float* em_rbar,
+                              cudaStream_t st);
+cudaError_t build_gather(spect_plan_s& P, cudaStream_t st);
+cudaError_t launch_adj_gather(const spect_plan_s& P, int l0, int nv, float* out, int accumulate, EmArgs em,
                               cudaStream_t st);
 cudaError_t launch_adj_rot_t(const spect_plan_s& P, int l0, int nv, float* out, int accumulate, EmArgs em,
                              cudaStream_t st);
