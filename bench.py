@@ -169,6 +169,7 @@ def run_ours(args):
 
     prob, plan, x0_h, y_h, rbar_h = make_workload(device, args.path, args.nview)
     info = plan.info()
+    launch_shape = plan.tuning if info["fused"] else None
     sep = info["separable"]
     chunk = info["view_chunk"]
     y = torch.from_numpy(y_h).to(device)
@@ -296,7 +297,7 @@ def run_ours(args):
                                       "anisotropic Gaussian PSF (separable factors), MLEM step with 10% smoothed "
                                       "background, XCAT-like ellipsoid phantom (seed 0)",
                           "path": args.path, "fused": info["fused"], "view_chunk": chunk, "nview": args.nview, "parallelism": f"replicas{world}",
-                          "launch_shape": plan.tuning if info["fused"] else None,
+                          "launch_shape": launch_shape,
                           "l2": "flushed between timed steps (256 MB write)",
                           "step": "one EM iteration = one A + one A' + fused ratio/update"},
                "clocks": clk.summary(), "gpu_launches": n_launch, "e2e": e2e, "roofline": roofline,

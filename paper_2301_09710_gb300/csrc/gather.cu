@@ -141,6 +141,17 @@ __global__ void __launch_bounds__(kGT) k_adj_gather(const __grid_constant__ CUte
     }
     __syncthreads();
 
+    // the EM epilogue's operands, fetched before the view loop so their latency hides behind it
+    const int k = kc0 + 4 * k4;
+    const bool mine = qi < g.nx && qj < g.ny && k < g.nz;
+    const size_t o = mine ? (size_t)(qj * g.nx + qi) * g.nz + k : 0;
+    float4 ex = make_float4(0.f, 0.f, 0.f, 0.f), es = ex, eu = ex;
+    if (mine && em.x) {
+        ex = *reinterpret_cast<const float4*>(em.x + o);
+        es = *reinterpret_cast<const float4*>(em.s + o);
+        if (em.u) eu = *reinterpret_cast<const float4*>(em.u + o);
+    }
+
     KSum acc[4];
     for (int v = 0; v < a.nv; ++v) {
         const int s = v % kStages;
@@ -179,14 +190,13 @@ __global__ void __launch_bounds__(kGT) k_adj_gather(const __grid_constant__ CUte
         }
     }
 
-    const int k = kc0 + 4 * k4;
-    if (qi >= g.nx || qj >= g.ny || k >= g.nz) return;
-    const size_t o = (size_t)(qj * g.nx + qi) * g.nz + k;
+    if (!mine) return;
+    const float xv[4] = {ex.x, ex.y, ex.z, ex.w}, sv4[4] = {es.x, es.y, es.z, es.w}, uv[4] = {eu.x, eu.y, eu.z, eu.w};
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         float val = acc[u].value();
         if (accumulate) val += out[o + u];
-        if (em.x) em.x[o + u] = em_update(em.x[o + u], val, em.s[o + u], em.u ? em.u[o + u] : 0.f, em.beta);
+        if (em.x) em.x[o + u] = em_update(xv[u], val, sv4[u], uv[u], em.beta);
         else out[o + u] = val;
     }
 }
