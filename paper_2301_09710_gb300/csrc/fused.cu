@@ -828,6 +828,264 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
 #undef SPECT_MBYTES
 }
 
+// ============================================================================
+// Fused blur for a full (non-separable) PSF p(a, b, j, l), padded tap count P.
+// The 2D convolution of a plane is a sum over tap rows b of 1D FIRs along i
+// (taps p(:, b)) applied to row k - b + cz: every term of a row runs through
+// the register-blocked FIR of the separable kernels, and the rows add up per
+// output (a row partial per b, then the sum over b: short FP32 chains).
+//   forward: the rotated planes come from k_rot_fwd (same images as the
+//     separable path: W[k][C + i] with replicate halo columns); ZH replicate
+//     halo rows above and below are filled in shared memory after each TMA
+//     load; outputs accumulate over the group's planes in ACC[i][k].
+//   adjoint: the detector plane is staged once per block, zero-padded
+//     (Vx[ZH + k][C + i]); per plane the taps of the k edge class of each
+//     output row are used for the whole run, and the first / last detector
+//     column (the i edge classes) is recomputed with its own variant.
+// ============================================================================
+__host__ __device__ inline int dir_rows(int nz, int ZH) { return nz + 2 * ZH; }
+
+__host__ __device__ inline size_t dir_fwd_smem_floats(const FusedDims& d, int nz, int P, int PT, int ZH)
+{
+    const size_t xarea = ((size_t)dir_rows(nz, ZH) * d.wp + 3) & ~(size_t)3;
+    // Wext x2 | taps P x PT | ACC | 2 mbarriers
+    return 2 * xarea + (size_t)P * PT + (size_t)d.urows * d.apc + 8;
+}
+
+__host__ __device__ inline size_t dir_adj_smem_floats(const FusedDims& d, int nz, int P, int PT, int ZH, int ncls)
+{
+    const size_t xarea = ((size_t)dir_rows(nz, ZH) * d.wp + 3) & ~(size_t)3;
+    // Vx | MB x2 | taps ncls x P x PT | 2 mbarriers
+    return xarea + 2 * (size_t)d.marea + (size_t)ncls * P * PT + 8;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_dir_fused(Geometry g, FusedDims d,
+                                                                     const float* __restrict__ wsl,
+                                                                     const float* __restrict__ psf,
+                                                                     float* __restrict__ part, int l0, int* err)
+{
+    using S = Sep<P>;
+    constexpr int C = S::C, CX = S::CX, ZH = S::ZH, PT = S::PT;
+    extern __shared__ __align__(16) float sm[];
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int xarea = (dir_rows(nz, ZH) * d.wp + 3) & ~3;
+    float* WB = sm;                                 // [2][xarea]: rows -ZH .. nz+ZH-1 of a plane image
+    float* TAP = WB + 2 * (size_t)xarea;            // [P][PT], this plane's taps (zero-padded, centred)
+    float* ACC = TAP + (size_t)P * PT;              // [i][k], apc pitch
+    uint64_t* bar = reinterpret_cast<uint64_t*>(ACC + (size_t)d.urows * d.apc);
+    const int tid = threadIdx.x;
+    constexpr int T = kFusedThreads;
+    const int grp = blockIdx.x, v = blockIdx.y, l = l0 + v;
+    const int lp = g.nvp == 1 ? 0 : l;
+    const int j_begin = grp * d.J, j_end = min(ny, j_begin + d.J);
+    const int ox = (P - g.px) / 2, oz = (P - g.pz) / 2;
+    const int pln = nx * nz;
+    const float* wv = wsl + (size_t)v * ny * d.parea;
+
+    for (int e = tid; e < d.urows * d.apc; e += T) ACC[e] = 0.f;
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tma_load_1d(WB + ZH * d.wp, wv + (size_t)j_begin * d.parea, (unsigned)d.warea * 4u, bar);
+        if (j_begin + 1 < j_end)
+            tma_load_1d(WB + xarea + ZH * d.wp, wv + (size_t)(j_begin + 1) * d.parea, (unsigned)d.warea * 4u,
+                        bar + 1);
+    }
+    __syncthreads();
+
+    unsigned phases = 0u;
+    for (int j = j_begin; j < j_end; ++j) {
+        const int b = (j - j_begin) & 1;
+        float* W = WB + b * (size_t)xarea;
+        const bool ok = mbar_wait_bounded(bar + b, (phases >> b) & 1u);
+        phases ^= 1u << b;
+        // this plane's taps, and the replicate halo rows (copies of rows 0 and nz-1)
+        const float* pp = psf + ((size_t)lp * ny + j) * g.px * g.pz;
+        for (int e = tid; e < P * PT; e += T) {
+            const int bb = e / PT, a = e - bb * PT, ax = a - ox, bz = bb - oz;
+            TAP[e] = (ax >= 0 && ax < g.px && bz >= 0 && bz < g.pz) ? __ldg(pp + (size_t)bz * g.px + ax) : 0.f;
+        }
+        if (ok)
+            for (int e = tid; e < 2 * C * d.wp; e += T) {
+                const int r = e / d.wp, c = e - r * d.wp;
+                if (r < C) W[(ZH - C + r) * d.wp + c] = W[ZH * d.wp + c];
+                else W[(ZH + nz + r - C) * d.wp + c] = W[(ZH + nz - 1) * d.wp + c];
+            }
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                flag_timeout(err);
+                mbar_wait_bounded(bar + b, ((phases >> b) & 1u) ^ 1u);
+                mbar_wait_bounded(bar + (b ^ 1), (phases >> (b ^ 1)) & 1u);
+            }
+            return;
+        }
+        // c_j(i, k) = sum_b FIR_i(taps p(:, b), row k - b + cz); lanes over k
+        for (int it = tid; it < nz * d.nib; it += T) {
+            const int ib = it / nz, k = it - ib * nz;
+            const int li = ib * CX;
+            float o[CX];
+#pragma unroll
+            for (int c = 0; c < CX; ++c) o[c] = 0.f;
+            for (int bb = 0; bb < P; ++bb) {
+                const float* wr = W + (ZH + k - bb + C) * d.wp + li;
+                float win[CX + P - 1];
+#pragma unroll
+                for (int m = 0; m < CX + P - 1; ++m) win[m] = wr[m];
+                float ob[CX];
+                fir<P, CX, -1, P - 1>(TAP + bb * PT, win, ob);
+#pragma unroll
+                for (int c = 0; c < CX; ++c) o[c] += ob[c];
+            }
+            float* ac = ACC + li * d.apc + k;
+            if (li + CX <= nx) {
+#pragma unroll
+                for (int c = 0; c < CX; ++c) ac[c * d.apc] += o[c];
+            } else {
+#pragma unroll
+                for (int c = 0; c < CX; ++c)
+                    if (li + c < nx) ac[c * d.apc] += o[c];
+            }
+        }
+        __syncthreads();  // buffer b and the taps are free
+        if (tid == 0 && j + 2 < j_end) {
+            fence_proxy_async_smem();
+            tma_load_1d(W + ZH * d.wp, wv + (size_t)(j + 2) * d.parea, (unsigned)d.warea * 4u, bar + b);
+        }
+    }
+    float* pout = part + ((size_t)grp * g.nview + l) * pln;
+    for (int e = tid; e < pln; e += T) {
+        const int k = e / nx, i = e - k * nx;
+        pout[e] = ACC[i * d.apc + k];
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kFusedThreads, 1) k_adj_dir_fused(Geometry g, FusedDims d, int cls_z,
+                                                                     const float* __restrict__ vin,
+                                                                     const float* __restrict__ mubar,
+                                                                     const float* __restrict__ psf_adj,
+                                                                     float* __restrict__ slab, int l0, int* err)
+{
+    using S = Sep<P>;
+    constexpr int C = S::C, CX = S::CX, ZH = S::ZH, PT = S::PT;
+    extern __shared__ __align__(16) float sm[];
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int xarea = (dir_rows(nz, ZH) * d.wp + 3) & ~3;
+    const int ncls = 3 * cls_z;                    // edge classes (ci, ck)
+    float* Vx = sm;                                // zero-padded detector plane, Vx[ZH + k][C + i]
+    float* MB = Vx + xarea;                        // [2][marea]
+    float* TAP = MB + 2 * (size_t)d.marea;         // [ci * cls_z + ck][P][PT], this plane
+    uint64_t* bar = reinterpret_cast<uint64_t*>(TAP + (size_t)ncls * P * PT);
+    const int tid = threadIdx.x;
+    constexpr int T = kFusedThreads;
+    const int grp = blockIdx.x, v = blockIdx.y, l = l0 + v;
+    const int lp = g.nvp == 1 ? 0 : l;
+    const int j_begin = grp * d.J, j_end = min(ny, j_begin + d.J);
+    const int ox = (P - g.px) / 2, oz = (P - g.pz) / 2;
+    const size_t nrow = (size_t)g.nvp * ny, pplane = (size_t)g.px * g.pz;
+    const int pln = nx * nz;
+    const float* mub = mubar + ((size_t)l * ny) * d.ps;
+    float* tsl = slab + ((size_t)v * ny) * d.ps;
+    const unsigned mbytes = (unsigned)d.ps * 4u;
+
+    for (int e = tid; e < xarea; e += T) Vx[e] = 0.f;
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tma_load_1d(MB, mub + (size_t)j_begin * d.ps, mbytes, bar);
+    }
+    __syncthreads();
+    for (int e = tid; e < pln; e += T) {
+        const int k = e / nx, i = e - k * nx;
+        Vx[(ZH + k) * d.wp + C + i] = vin[(size_t)l * pln + e];
+    }
+
+    unsigned phases = 0u;
+    for (int j = j_begin; j < j_end; ++j) {
+        const int b = (j - j_begin) & 1;
+        // taps of every edge class of this plane
+        for (int e = tid; e < ncls * P * PT; e += T) {
+            const int cls = e / (P * PT), r = e - cls * P * PT, bb = r / PT, a = r - bb * PT;
+            const int ax = a - ox, bz = bb - oz;
+            TAP[e] = (ax >= 0 && ax < g.px && bz >= 0 && bz < g.pz)
+                         ? __ldg(psf_adj + ((size_t)cls * nrow + (size_t)lp * ny + j) * pplane + (size_t)bz * g.px + ax)
+                         : 0.f;
+        }
+        __syncthreads();
+        // the other buffer receives the next plane's attenuation once its store has read it
+        if (tid == 0 && j + 1 < j_end) {
+            tma_store_wait_read<0>();
+            tma_load_1d(MB + (b ^ 1) * (size_t)d.marea, mub + (size_t)(j + 1) * d.ps, mbytes, bar + (b ^ 1));
+        }
+        float* mb = MB + b * (size_t)d.marea;
+        const bool ok = mbar_wait_bounded(bar + b, (phases >> b) & 1u);
+        phases ^= 1u << b;
+        if (ok) {
+            for (int it = tid; it < nz * d.nib; it += T) {
+                const int ib = it / nz, k = it - ib * nz;
+                const int li = ib * CX;
+                const int ck = nz == 1 ? 0 : (k == 0 ? 1 : (k == nz - 1 ? 2 : 0));
+                const float* TK = TAP + (size_t)ck * P * PT;  // class (ci = interior, ck)
+                float o[CX];
+#pragma unroll
+                for (int c = 0; c < CX; ++c) o[c] = 0.f;
+                for (int bb = 0; bb < P; ++bb) {
+                    const float* vr = Vx + (ZH + k + bb - C) * d.wp + li;
+                    float win[CX + P - 1];
+#pragma unroll
+                    for (int m = 0; m < CX + P - 1; ++m) win[m] = vr[m];
+                    float ob[CX];
+                    fir<P, CX, 1, 0>(TK + bb * PT, win, ob);
+#pragma unroll
+                    for (int c = 0; c < CX; ++c) o[c] += ob[c];
+                }
+                // first / last detector column: their own edge-class variant
+                const int cl = nx - 1 - li;
+                if (li == 0 || cl < CX) {
+                    auto edge = [&](int c, int ci) {
+                        const float* TC = TAP + (size_t)(ci * cls_z + ck) * P * PT;
+                        float acc = 0.f;
+                        for (int bb = 0; bb < P; ++bb) {
+                            const float* vr = Vx + (ZH + k + bb - C) * d.wp + li + c;
+                            float rp = 0.f;
+#pragma unroll
+                            for (int a = 0; a < P; ++a) rp = fmaf(TC[bb * PT + a], vr[a], rp);
+                            acc += rp;
+                        }
+                        return acc;
+                    };
+                    if (li == 0) o[0] = edge(0, 1);
+                    if (cl < CX) {
+#pragma unroll
+                        for (int c = 0; c < CX; ++c)
+                            if (c == cl) o[c] = edge(c, nx == 1 ? 0 : 2);
+                    }
+                }
+                float* mp = mb + li * nz + k;
+#pragma unroll
+                for (int c = 0; c < CX; ++c)
+                    if (li + c < nx) mp[c * nz] = o[c] * mp[c * nz];
+            }
+        }
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                flag_timeout(err);
+                mbar_wait_bounded(bar + b, ((phases >> b) & 1u) ^ 1u);
+                tma_store_wait_all();
+            }
+            return;
+        }
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            tma_store_1d(tsl + (size_t)j * d.ps, mb, mbytes);
+        }
+    }
+    if (tid == 0) tma_store_wait_all();
+}
+
 // x_t(q,k) (+)= sum_{v in chunk} sum_{e < MAXE} w_e t[v][p_e][k]
 // with the EM update (em_update) on the last chunk when em.x is set.  The
 // lists are laid out [q][l][e] so one destination's entries for all views are
@@ -1042,6 +1300,72 @@ cudaError_t adj_launch(const spect_plan_s& Pl, const float* v, int l0, int nv, c
 }
 }  // namespace
 
+namespace {
+template <int P>
+size_t dir_smem_fwd(const Geometry& g, const FusedDims& d)
+{
+    return dir_fwd_smem_floats(d, g.nz, P, Sep<P>::PT, Sep<P>::ZH) * sizeof(float);
+}
+
+template <int P>
+size_t dir_smem_adj(const Geometry& g, const FusedDims& d, int cls_z)
+{
+    return dir_adj_smem_floats(d, g.nz, P, Sep<P>::PT, Sep<P>::ZH, 3 * cls_z) * sizeof(float);
+}
+
+template <int P>
+bool dir_fits(const Geometry& g, size_t limit, int J, int adj_J)
+{
+    const int cls_z = g.nz >= 2 ? 3 : 1;
+    const FusedDims df = dims_for<P>(g, J, 1), da = dims_for<P>(g, adj_J, 1);
+    return df.nT == 1 && dir_smem_fwd<P>(g, df) <= limit && dir_smem_adj<P>(g, da, cls_z) <= limit &&
+           (size_t)df.farea * 4 <= limit && (size_t)df.ps * 4 < (1u << 20);
+}
+
+template <int P>
+cudaError_t dir_fwd_launch(const spect_plan_s& Pl, int l0, int nv, cudaStream_t st)
+{
+    const FusedDims d = dims_for<P>(Pl.g, Pl.fused_J, 1);
+    const size_t smem = dir_smem_fwd<P>(Pl.g, d);
+    cudaError_t e = cudaFuncSetAttribute(k_fwd_dir_fused<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_fwd_dir_fused<P><<<dim3(d.G, nv), kFusedThreads, smem, st>>>(Pl.g, d, Pl.slab, Pl.psf, Pl.part, l0, Pl.err);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t dir_adj_launch(const spect_plan_s& Pl, const float* v, int l0, int nv, cudaStream_t st)
+{
+    const FusedDims d = dims_for<P>(Pl.g, Pl.adj_J, 1);
+    const size_t smem = dir_smem_adj<P>(Pl.g, d, Pl.cls_z);
+    cudaError_t e = cudaFuncSetAttribute(k_adj_dir_fused<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_adj_dir_fused<P><<<dim3(d.G, nv), kFusedThreads, smem, st>>>(Pl.g, d, Pl.cls_z, v, Pl.mubar, Pl.psf_adj,
+                                                                    Pl.slab, l0, Pl.err);
+    return cudaGetLastError();
+}
+}  // namespace
+
+// Bucket of the fused full-PSF kernels (untiled planes only), 0 when they do not fit.
+int fused_dir_bucket(const Geometry& g, size_t smem_limit)
+{
+    const int p = g.px > g.pz ? g.px : g.pz;
+    for (int b : kBuckets) {
+        if (b < p) continue;
+        bool ok = false;
+        switch (b) {
+#define SPECT_DF(B) \
+    case B: ok = dir_fits<B>(g, smem_limit, 8, 8); break;
+            SPECT_DF(3) SPECT_DF(5) SPECT_DF(7) SPECT_DF(9) SPECT_DF(11) SPECT_DF(13) SPECT_DF(15)
+            SPECT_DF(17) SPECT_DF(21) SPECT_DF(25) SPECT_DF(29) SPECT_DF(33) SPECT_DF(37)
+#undef SPECT_DF
+            default: break;
+        }
+        return ok ? b : 0;
+    }
+    return 0;
+}
+
 int fused_bucket(const Geometry& g, size_t smem_limit, int* tiles)
 {
     const int p = g.px > g.pz ? g.px : g.pz;
@@ -1089,6 +1413,19 @@ int fused_tiles_fit(const Geometry& g, int bucket, int J, int adj_J, int tiles, 
     }
 }
 
+// Whether the fused full-PSF kernels fit with depth groups J / adj_J.
+bool fused_dir_fit(const Geometry& g, int bucket, int J, int adj_J, size_t smem_limit)
+{
+    switch (bucket) {
+#define SPECT_DF(B) \
+    case B: return dir_fits<B>(g, smem_limit, J, adj_J);
+        SPECT_DF(3) SPECT_DF(5) SPECT_DF(7) SPECT_DF(9) SPECT_DF(11) SPECT_DF(13) SPECT_DF(15)
+        SPECT_DF(17) SPECT_DF(21) SPECT_DF(25) SPECT_DF(29) SPECT_DF(33) SPECT_DF(37)
+#undef SPECT_DF
+        default: return false;
+    }
+}
+
 int fused_groups(const spect_plan_s& P) { return (P.g.ny + P.fused_J - 1) / P.fused_J; }
 
 #define SPECT_DISPATCH(FN, ...)                        \
@@ -1111,6 +1448,9 @@ int fused_groups(const spect_plan_s& P) { return (P.g.ny + P.fused_J - 1) / P.fu
 
 cudaError_t launch_fused_forward(const spect_plan_s& P, const float* xt, int l0, int nv, cudaStream_t st)
 {
+    if (!P.separable) {
+        SPECT_DISPATCH(dir_fwd_launch, P, l0, nv, st)
+    }
     SPECT_DISPATCH(fwd_launch, P, xt, l0, nv, st)
 }
 
@@ -1145,6 +1485,9 @@ size_t fused_slab_per_view(const spect_plan_s& P)
 
 cudaError_t launch_fused_adjoint(const spect_plan_s& P, const float* v, int l0, int nv, cudaStream_t st)
 {
+    if (!P.separable) {
+        SPECT_DISPATCH(dir_adj_launch, P, v, l0, nv, st)
+    }
     SPECT_DISPATCH(adj_launch, P, v, l0, nv, st)
 }
 #undef SPECT_DISPATCH

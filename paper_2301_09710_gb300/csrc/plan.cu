@@ -393,6 +393,10 @@ spect_status spect_plan_bytes(int nx, int ny, int nz, int nview, int px, int pz,
     if (P.separable && !(flags & SPECT_PLAN_LOW_MEMORY)) {
         P.bucket = spect::fused_bucket(g, (size_t)smem_optin, &P.fused_nT);
         P.fast = P.bucket > 0;
+    } else if (!(flags & SPECT_PLAN_LOW_MEMORY)) {
+        P.bucket = spect::fused_dir_bucket(g, (size_t)smem_optin);
+        P.fast = P.bucket > 0;
+        P.fused_nT = 1;
     }
     *bytes = plan_bytes_bound(P);
     return SPECT_OK;
@@ -472,6 +476,11 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
     if (P->separable && !(flags & SPECT_PLAN_LOW_MEMORY)) {
         P->bucket = spect::fused_bucket(g, (size_t)smem_optin, &P->fused_nT);
         P->fast = P->bucket > 0;
+    } else if (!(flags & SPECT_PLAN_LOW_MEMORY)) {
+        // full PSF: the fused full-PSF blur kernels, untiled planes only
+        P->bucket = spect::fused_dir_bucket(g, (size_t)smem_optin);
+        P->fast = P->bucket > 0;
+        P->fused_nT = 1;
     }
     if (P->separable) {
         P->sep_tk = spect::choose_sep_tile(g, P->cls_z, (size_t)smem_optin);
@@ -864,7 +873,8 @@ spect_status reconfigure(spect_plan_s* P, int J, int adj_J, int tiles, cudaStrea
         cudaGetLastError();
         return fail(SPECT_ECUDA, "device query failed");
     }
-    const int nt = spect::fused_tiles_fit(g, P->bucket, J, adj_J, tiles, (size_t)smem);
+    const int nt = P->separable ? spect::fused_tiles_fit(g, P->bucket, J, adj_J, tiles, (size_t)smem)
+                                : (tiles == 1 && spect::fused_dir_fit(g, P->bucket, J, adj_J, (size_t)smem) ? 1 : 0);
     if (nt == 0) return fail(SPECT_EUNSUPPORTED, "this launch shape does not fit shared memory");
     const int oJ = P->fused_J, oaJ = P->adj_J, ont = P->fused_nT;
     P->fused_J = J;
@@ -967,6 +977,7 @@ spect_status spect_plan_autotune(spect_plan P, spect_stream stream)
     std::vector<int> tile_cands;
     for (int t : {base, base + 1, 2 * base, 4 * base})
         if (t <= nib && std::find(tile_cands.begin(), tile_cands.end(), t) == tile_cands.end()) tile_cands.push_back(t);
+    if (!P->separable) tile_cands.assign(1, 1);  // the full-PSF kernels run untiled
     std::vector<int> Js;
     for (int J : {4, 8, 16})
         if (J <= std::max(g.ny, 4)) Js.push_back(J);

@@ -317,6 +317,9 @@ int choose_sep_tile(const Geometry& g, int cls_z, size_t smem_limit);
 // they do not fit; *tiles receives the column-tile count they need.
 int fused_bucket(const Geometry& g, size_t smem_limit, int* tiles);
 int fused_groups(const spect_plan_s& P);
+// Bucket of the fused full-PSF kernels (untiled planes), 0 when they do not fit.
+int fused_dir_bucket(const Geometry& g, size_t smem_limit);
+bool fused_dir_fit(const Geometry& g, int bucket, int J, int adj_J, size_t smem_limit);
 int fused_tiles_fit(const Geometry& g, int bucket, int J, int adj_J, int tiles, size_t smem_limit);
 cudaError_t launch_transpose(const float* in, float* out, int R, int C, cudaStream_t st);
 cudaError_t launch_mubar_cache(const spect_plan_s& P, const float* mu_t, cudaStream_t st);

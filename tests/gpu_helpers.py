@@ -38,9 +38,9 @@ def host(t):
     return t.detach().cpu().numpy().astype(np.float64)
 
 
-# the three code paths of the library: fused kernels (separable PSF, default),
-# low-memory kernels (separable PSF), full-PSF kernels
-PATHS = ["fused", "lowmem", "direct"]
+# the code paths of the library: fused kernels (separable PSF, default),
+# low-memory kernels (separable PSF), fused full-PSF kernels, low-memory full-PSF kernels
+PATHS = ["fused", "lowmem", "direct", "direct_lowmem"]
 
 
 def make_plan(prob, angles, path, nview=None):
@@ -51,7 +51,8 @@ def make_plan(prob, angles, path, nview=None):
     if path in ("fused", "lowmem", True):
         return SpectPlan(nx, nz, nview, mu=prob.mu, dy=prob.dy, fx=prob.fx, fz=prob.fz, angles=angles,
                          low_memory=(path == "lowmem"))
-    return SpectPlan(nx, nz, nview, mu=prob.mu, dy=prob.dy, psf=prob.full_psf(), angles=angles)
+    return SpectPlan(nx, nz, nview, mu=prob.mu, dy=prob.dy, psf=prob.full_psf(), angles=angles,
+                     low_memory=(path == "direct_lowmem"))
 
 
 def oracle_psf(prob, path):

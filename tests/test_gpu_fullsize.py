@@ -30,7 +30,7 @@ def prob():
 def test_config2_sampled_views(prob, path):
     ang = oracle.default_angles(128)
     plan = make_plan(prob, ang, path)
-    assert plan.info()["fused"] == (path == "fused")
+    assert plan.info()["fused"] == (path in ("fused", "direct"))
     x = dev(prob.x)
     v = host(plan.forward(x))
     psf = oracle_psf(prob, path)

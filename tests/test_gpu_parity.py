@@ -27,7 +27,8 @@ def test_config1_forward_back_em(path):
     ang = oracle.default_angles(prob.nview)
     psf = oracle_psf(prob, path)
     plan = make_plan(prob, ang, path)
-    assert plan.info()["separable"] == (path != "direct")
+    assert plan.info()["separable"] == (path in ("fused", "lowmem"))
+    assert plan.info()["fused"] == (path in ("fused", "direct"))
     x = dev(prob.x)
     v = plan.forward(x)
     v_o = oracle.forward(prob.x, prob.mu, psf, prob.dy, ang)
