@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--direct-steps", type=int, default=3, help="steps of the full-PSF path reported beside (0: skip)")
     ap.add_argument("--cpu-views", type=int, default=0, help="views in the CPU baseline sample (0: auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default launch shapes")
     ap.add_argument("--nview", type=int, default=NVIEW,
                     help="views of the workload (default 128; fewer only for small profiler captures)")
     return ap.parse_args()
@@ -104,7 +105,7 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- workload
-def make_workload(device, path, nview=NVIEW):
+def make_workload(device, path, nview=NVIEW, autotune=True):
     import torch
 
     from paper_2301_09710_gb300 import SpectPlan, synthetic
@@ -113,7 +114,8 @@ def make_workload(device, path, nview=NVIEW):
     sep = path == "separable"
     if sep:
         plan = SpectPlan(NX, NZ, nview, mu=prob.mu, dy=prob.dy, fx=prob.fx, fz=prob.fz, device=device)
-        plan.autotune()  # the library's launch-shape autotuner (timed on this device, outside the timed region)
+        if autotune:
+            plan.autotune()  # the library's launch-shape autotuner (timed on this device, outside the timed region)
     else:
         plan = SpectPlan(NX, NZ, nview, mu=prob.mu, dy=prob.dy, psf=prob.full_psf(), device=device)
     xt = torch.from_numpy(prob.x).to(device)
@@ -142,6 +144,11 @@ def algorithmic_flops(kind: str, nv: float, sep: bool, fused: bool = False) -> f
     return per * vv
 
 
+# DRAM bytes (read + write) per 128-view launch of the fused separable kernels, from one ncu capture of the
+# 32-view case scaled by 4 (profiles/fused_kernels_128x128x80_32views.md); valid for the kernels as captured.
+NCU_TRAFFIC_BYTES_128 = {"conv_adj": 1161.4e6, "conv_fwd": 896.7e6, "rotate_atten": 1409.4e6, "rotate_adj": 1111.6e6}
+
+
 def peaks(torch, dev_index):
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     mp = json.load(open(path)) if os.path.exists(path) else {}
@@ -167,7 +174,7 @@ def run_ours(args):
     from __graft_entry__ import build
     build()
 
-    prob, plan, x0_h, y_h, rbar_h = make_workload(device, args.path, args.nview)
+    prob, plan, x0_h, y_h, rbar_h = make_workload(device, args.path, args.nview, autotune=not args.no_autotune)
     info = plan.info()
     launch_shape = plan.tuning if info["fused"] else None
     sep = info["separable"]
@@ -234,7 +241,10 @@ def run_ours(args):
     dom = max(kern, key=lambda k: kern[k]["ms_total"])
     achieved = kern[dom]["tflops"]
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
-                "frac": (achieved / pk["fp32_tflops"]) if achieved else None, "traffic": None,
+                "frac": (achieved / pk["fp32_tflops"]) if achieved else None,
+                "traffic": (NCU_TRAFFIC_BYTES_128.get(dom) * args.nview / 128.0
+                            if sep and info["fused"] and dom in NCU_TRAFFIC_BYTES_128 else None),
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "peak_basis": f"{pk['sms']} SMs x 128 FP32 lanes x 2 FLOP x {pk['sm_max_mhz']:.0f} MHz (max SM clock)",
                 "probe_tflops": probe,
                 "kernels": kern}
