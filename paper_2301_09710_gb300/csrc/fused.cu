@@ -1456,6 +1456,8 @@ cudaError_t launch_fused_forward(const spect_plan_s& P, const float* xt, int l0,
 
 cudaError_t launch_fused_rotate(const spect_plan_s& P, const float* xt, int l0, int nv, cudaStream_t st)
 {
+    // untiled planes read from the plan's own x_t: the patch-staged rotation (rotpatch.cu)
+    if (P.rotpatch && P.rotpatch_on && P.fused_nT == 1 && xt == P.xt) return launch_rot_patch(P, l0, nv, st);
     SPECT_DISPATCH(rot_launch, P, xt, l0, nv, st)
 }
 

@@ -84,16 +84,6 @@ __global__ void k_patch_entries(Geometry g, int ps, int maxe, const AdjEntry* __
     }
 }
 
-__device__ __forceinline__ void tma_load_3d(void* dst_smem, const CUtensorMap* map, int c0, int c1, int c2,
-                                            uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];" ::"r"(smem_u32(dst_smem)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
-        : "memory");
-}
-
 struct GatherArgs {
     Geometry g;
     int npx;         // patches along i
@@ -201,9 +191,16 @@ __global__ void __launch_bounds__(kGT) k_adj_gather(const __grid_constant__ CUte
     }
 }
 
-using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// floats per pipeline stage: the box, then the entries, rounded up to 128 bytes
+int stage_floats(int box_floats, int ent_bytes) { return (box_floats + ent_bytes / 4 + 31) & ~31; }
+
+size_t gather_smem(int box_floats, int ent_bytes)
+{
+    return (size_t)kStages * stage_floats(box_floats, ent_bytes) * sizeof(float) + kStages * sizeof(uint64_t);
+}
+
+}  // namespace
 
 EncodeTiled encode_fn()
 {
@@ -219,16 +216,6 @@ EncodeTiled encode_fn()
     }
     return fn;
 }
-
-// floats per pipeline stage: the box, then the entries, rounded up to 128 bytes
-int stage_floats(int box_floats, int ent_bytes) { return (box_floats + ent_bytes / 4 + 31) & ~31; }
-
-size_t gather_smem(int box_floats, int ent_bytes)
-{
-    return (size_t)kStages * stage_floats(box_floats, ent_bytes) * sizeof(float) + kStages * sizeof(uint64_t);
-}
-
-}  // namespace
 
 int gather_kc() { return 16; }
 

@@ -134,7 +134,7 @@ void free_plan(spect_plan_s* P, cudaStream_t st)
     for (cudaEvent_t e : P->evpool) cudaEventDestroy(e);
     void* ptrs[] = {P->mu, P->psf, P->psf_adj, P->fx, P->fz, P->fx_adj, P->fz_adj, P->rot, P->adj_off, P->adj,
                     P->slab, P->e, P->ratio, P->s, P->mubar, P->xt, P->et, P->st, P->part, P->adjf, P->err, P->rtab, P->ut,
-                    P->gboxes, P->gent};
+                    P->gboxes, P->gent, P->rboxes};
     for (void* p : ptrs) raw_free(P, p, st);
     delete P;
 }
@@ -358,7 +358,7 @@ size_t plan_bytes_bound(const spect_plan_s& P)
         b += nproj * (size_t)spect::fused_groups(P) * F + (size_t)g.nview * g.ny * P.ts * F;
         // patch gather: boxes and box-local entries (at most 8 per list)
         const size_t np = (size_t)((g.nx + 7) / 8) * ((g.ny + 7) / 8) * g.nview;
-        b += np * 16 + np * 64 * 8 * sizeof(spect::AdjEntry);
+        b += np * 16 + np * 64 * 8 * sizeof(spect::AdjEntry) + np * 16;  // + rotation boxes
     }
     return b;
 }
@@ -622,6 +622,7 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
         PLAN_ALLOC(P->rtab, (size_t)nview * ny * P->ts, "rotation tables");
         PLAN_TRY(spect::launch_rot_tables(*P, st), "rotation table launch");
         PLAN_TRY(spect::build_gather(*P, st), "patch gather set-up");
+        PLAN_TRY(spect::build_rotpatch(*P, st), "patch rotation set-up");
     }
     PLAN_TRY(cudaStreamSynchronize(st), "plan set-up");
     *out = P;
@@ -927,7 +928,7 @@ spect_status time_best(cudaStream_t st, int reps, float* best, F&& fn)
 }
 
 struct Tuned {
-    int J, adj_J, tiles;
+    int J, adj_J, tiles, rotpatch;
 };
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int, int, int>, Tuned> g_tuned;  // per geometry and device
@@ -963,7 +964,10 @@ spect_status spect_plan_autotune(spect_plan P, spect_stream stream)
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(key);
-        if (it != g_tuned.end()) return reconfigure(P, it->second.J, it->second.adj_J, it->second.tiles, st);
+        if (it != g_tuned.end()) {
+            P->rotpatch_on = P->rotpatch && it->second.rotpatch;
+            return reconfigure(P, it->second.J, it->second.adj_J, it->second.tiles, st);
+        }
     }
     // inputs of the timed calls: the plan's own scratch (x_t = 1, v = 1)
     const size_t vol = (size_t)g.nx * g.ny * g.nz, nproj = (size_t)g.nx * g.nz * g.nview;
@@ -981,7 +985,8 @@ spect_status spect_plan_autotune(spect_plan P, spect_stream stream)
     std::vector<int> Js;
     for (int J : {4, 8, 16})
         if (J <= std::max(g.ny, 4)) Js.push_back(J);
-    Tuned best{P->fused_J, P->adj_J, base};
+    Tuned best{P->fused_J, P->adj_J, base, 0};
+    P->rotpatch_on = 0;
     float best_ms = 1e30f;
     spect_status r = SPECT_OK;
     for (int t : tile_cands) {
@@ -1008,9 +1013,18 @@ spect_status spect_plan_autotune(spect_plan P, spect_stream stream)
             best = {fJ, aJ, t};
         }
     }
+    if (r == SPECT_OK) r = reconfigure(P, best.J, best.adj_J, best.tiles, st);
+    // the rotation kernel: plane gathers or patch-staged boxes (untiled planes only)
+    if (r == SPECT_OK && P->rotpatch && P->fused_nT == 1) {
+        float ms_plane = 0.f, ms_patch = 0.f;
+        r = time_best(st, 3, &ms_plane, [&] { return fast_forward(P, P->xt, P->ratio, nullptr, nullptr, st); });
+        P->rotpatch_on = 1;
+        if (r == SPECT_OK)
+            r = time_best(st, 3, &ms_patch, [&] { return fast_forward(P, P->xt, P->ratio, nullptr, nullptr, st); });
+        P->rotpatch_on = r == SPECT_OK && ms_patch < ms_plane;
+        best.rotpatch = P->rotpatch_on;
+    }
     P->prof = prof;
-    if (r != SPECT_OK) return r;
-    r = reconfigure(P, best.J, best.adj_J, best.tiles, st);
     if (r != SPECT_OK) return r;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned[key] = best;

@@ -14,6 +14,7 @@
 //   back    : K2T blur-adjoint+attenuate v -> slab (t) then K1T adjoint-rotate+view-sum slab -> x
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -98,6 +99,13 @@ struct spect_plan_s {
     int4* gboxes = nullptr;      // [patch][l] source box (i0, j0, width, height)
     spect::AdjEntry* gent = nullptr;  // [patch][l][64][adj_max] box-local entries
     int gbw = 0, gbh = 0, gnpx = 0, gnpy = 0;
+    // patch-staged forward rotation (rotpatch.cu): available when rotpatch != 0,
+    // used instead of k_rot_fwd when rotpatch_on != 0 (chosen by the autotuner)
+    int rotpatch = 0;
+    int rotpatch_on = 0;
+    int4* rboxes = nullptr;      // [patch][l] source box of x_t (i0, j0, width, height)
+    int rbw = 0, rbh = 0;
+    CUtensorMap rmap_x, rmap_mu; // x_t (k, i, j) and the attenuation cache (k, i, plane)
     int ps = 0;                  // plane stride of the attenuation cache and slab: nx*nz rounded up to 4
     int ts = 0;                  // rotation table block per (view, row): 5*nx rounded up to 4
     float* rtab = nullptr;       // nview*ny*ts rotation tables of the fused forward
@@ -296,6 +304,24 @@ __device__ __forceinline__ void tma_store_wait_read()
 
 __device__ __forceinline__ void tma_store_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+// Tiled 3D tensor load (TMA) of the box at coordinates (c0, c1, c2) of `map`
+// into shared memory (128-byte aligned), completing on `bar`.
+__device__ __forceinline__ void tma_load_3d(void* dst_smem, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst_smem)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Host: cuTensorMapEncodeTiled through the runtime's driver entry point (NULL when unavailable).
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encode_fn();
+
 // --------------------------------------------------------------------- launchers
 // Host: per-view rotation constants for nview angles (NULL: 2 pi l / nview).
 void make_view_rot(int nx, int nview, const double* angles, ViewRot* out);
@@ -332,6 +358,8 @@ cudaError_t launch_fused_adjoint(const spect_plan_s& P, const float* v, int l0, 
 cudaError_t launch_fwd_reduce(const spect_plan_s& P, float* v, const float* em_y, const float* em_rbar,
                               cudaStream_t st);
 cudaError_t build_gather(spect_plan_s& P, cudaStream_t st);
+cudaError_t build_rotpatch(spect_plan_s& P, cudaStream_t st);
+cudaError_t launch_rot_patch(const spect_plan_s& P, int l0, int nv, cudaStream_t st);
 cudaError_t launch_adj_gather(const spect_plan_s& P, int l0, int nv, float* out, int accumulate, EmArgs em,
                               cudaStream_t st);
 cudaError_t launch_adj_rot_t(const spect_plan_s& P, int l0, int nv, float* out, int accumulate, EmArgs em,

@@ -233,3 +233,38 @@ def test_patch_gather_bitwise_equals_list_gather(case, monkeypatch):
     assert np.array_equal(host(xa), host(xr)), "EM through the patch gather differs"
     plan.check()
     ref.check()
+
+
+# ---------------------------------------------------------------- patch-staged forward rotation
+ROTP = [(48, 20, 7, 9, 31, "fused"), (33, 12, 9, 5, 32, "fused"), (64, 16, 24, 37, 33, "fused"),
+        (17, 4, 5, 3, 34, "fused"), (40, 8, 13, 11, 35, "direct"), (50, 36, 6, 7, 36, "fused")]
+
+
+@pytest.mark.parametrize("case", ROTP, ids=[f"{c[0]}x{c[1]}v{c[2]}p{c[3]}{c[5]}" for c in ROTP])
+def test_patch_rotation_bitwise_equals_plane_rotation(case, monkeypatch):
+    """The patch-staged rotation (x_t boxes and attenuation tiles by TMA) computes
+    every sample with the same weights, corners and arithmetic as the plane
+    gather: A x and the EM update are bitwise equal."""
+    nx, nz, nview, p, seed, path = case
+    prob = synthetic.random_problem(seed, nx=nx, nz=nz, nview=nview, px=p, pz=p, mu_scale=0.1)
+    rng = np.random.default_rng(seed)
+    ang = rng.uniform(0, 2 * np.pi, nview)
+    psf = oracle_psf(prob, path)
+    monkeypatch.setenv("SPECT_ROTPATCH", "1")  # patch rotation from the start
+    plan = make_plan(prob, ang, path)
+    monkeypatch.setenv("SPECT_ROTPATCH", "0")
+    ref = make_plan(prob, ang, path)
+    monkeypatch.delenv("SPECT_ROTPATCH")
+    assert plan.info()["device_bytes"] > ref.info()["device_bytes"]  # the patch boxes
+    x = dev(prob.x)
+    v = host(plan.forward(x))
+    assert np.array_equal(v, host(ref.forward(x))), "patch rotation differs from the plane rotation"
+    assert_close(v, oracle.forward(prob.x, prob.mu, psf, prob.dy, ang), what="A x (patch rotation)")
+    y = synthetic.poisson_counts(oracle.forward(prob.x, prob.mu, psf, prob.dy, ang) * 20, seed)
+    x0 = np.full(prob.x.shape, 0.5, np.float32)
+    xa, xr = dev(x0), dev(x0)
+    plan.em_step(xa, dev(y), None, niter=2)
+    ref.em_step(xr, dev(y), None, niter=2)
+    assert np.array_equal(host(xa), host(xr)), "EM through the patch rotation differs"
+    plan.check()
+    ref.check()
