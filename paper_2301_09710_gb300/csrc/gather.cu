@@ -28,7 +28,7 @@ namespace {
 
 constexpr int kGT = 256;      // threads: 64 destinations x 4 float4 groups of k
 constexpr int kPatch = 8;     // destinations per patch side
-constexpr int kStages = 4;    // views in flight per block
+constexpr int kStages = 3;    // views in flight per block (measured best: 3 of 3, 4, 6, 8)
 
 // Box of source pixels read by patch `patch` in view l: (i0, j0, width, height).
 __global__ void k_patch_boxes(Geometry g, int ps, int maxe, const AdjEntry* __restrict__ adjf, int npx, int4* boxes)
@@ -94,43 +94,72 @@ struct GatherArgs {
     int l0, nv;      // views [l0, l0 + nv) of the plan; slab view v holds view l0 + v
 };
 
+// Consumer threads: 64 destinations x 4 float4 groups of k; one more warp
+// produces: it refills a stage as soon as every consumer has released it
+// (per-stage "empty" barrier), so consumers never meet at a block barrier
+// inside the view loop.
 template <int MAXE>
-__global__ void __launch_bounds__(kGT) k_adj_gather(const __grid_constant__ CUtensorMap tmap, GatherArgs a,
-                                                    const int4* __restrict__ boxes, const AdjEntry* __restrict__ pent,
-                                                    float* out, int accumulate, EmArgs em, int* err)
+__global__ void __launch_bounds__(kGT + 32) k_adj_gather(const __grid_constant__ CUtensorMap tmap, GatherArgs a,
+                                                         const int4* __restrict__ boxes,
+                                                         const AdjEntry* __restrict__ pent, float* out,
+                                                         int accumulate, EmArgs em, int* err)
 {
     extern __shared__ __align__(128) float sm[];
     const Geometry& g = a.g;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + (size_t)kStages * a.stage_floats);
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + (size_t)kStages * a.stage_floats);
+    uint64_t* empty = full + kStages;
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kStages);
     const int patch = blockIdx.x, kc0 = blockIdx.y * a.kc;
     const int tid = threadIdx.x;
-    const int ql = tid >> 2, k4 = tid & 3;  // destination in the patch, float4 group of k
-    const int qi = (patch % a.npx) * kPatch + (ql % kPatch), qj = (patch / a.npx) * kPatch + (ql / kPatch);
+    const bool producer = tid >= kGT;
 
-    auto issue = [&](int v) {  // views in flight: stage v % kStages
-        const int s = v % kStages;
-        float* st = sm + (size_t)s * a.stage_floats;
-        const int l = a.l0 + v;
-        const int4 b = boxes[(size_t)patch * g.nview + l];
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar + s)),
-                     "r"((unsigned)(a.box_floats * 4 + a.ent_bytes))
-                     : "memory");
-        tma_load_3d(st, &tmap, kc0, b.x, v * g.ny + b.y, bar + s);
-        tma_copy_1d(st + a.box_floats, pent + ((size_t)patch * g.nview + l) * (kPatch * kPatch) * MAXE,
-                    (unsigned)a.ent_bytes, bar + s);
-    };
     // tensor copies want 128-byte aligned shared memory: refuse (error word) rather than fault
     if ((smem_u32(sm) & 127u) != 0) {
         if (tid == 0 && err) atomicExch(err, (int)SPECT_ECUDA);
         return;
     }
-    if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(bar + s, 1);
+    if (tid == kGT) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, kGT);
+        }
+        *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int v = 0; v < kStages && v < a.nv; ++v) issue(v);
     }
     __syncthreads();
 
+    if (producer) {
+        if (tid != kGT) return;  // one lane issues
+        int issued = 0;
+        for (int v = 0; v < a.nv; ++v) {
+            const int s = v % kStages;
+            if (*abort_flag) break;
+            if (v >= kStages && !mbar_wait_bounded(empty + s, (unsigned)(v / kStages - 1) & 1u)) {
+                *abort_flag = 1;
+                break;
+            }
+            if (v >= kStages) fence_proxy_async_smem();
+            float* st = sm + (size_t)s * a.stage_floats;
+            const int l = a.l0 + v;
+            const int4 b = boxes[(size_t)patch * g.nview + l];
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(full + s)),
+                         "r"((unsigned)(a.box_floats * 4 + a.ent_bytes))
+                         : "memory");
+            tma_load_3d(st, &tmap, kc0, b.x, v * g.ny + b.y, full + s);
+            tma_copy_1d(st + a.box_floats, pent + ((size_t)patch * g.nview + l) * (kPatch * kPatch) * MAXE,
+                        (unsigned)a.ent_bytes, full + s);
+            issued = v + 1;
+        }
+        if (*abort_flag) {  // let every copy in flight land before the block's shared memory is released
+            if (err) atomicExch(err, (int)SPECT_ETIMEOUT);
+            for (int u = issued - kStages < 0 ? 0 : issued - kStages; u < issued; ++u)
+                mbar_wait_bounded(full + (u % kStages), (unsigned)(u / kStages) & 1u);
+        }
+        return;
+    }
+
+    const int ql = tid >> 2, k4 = tid & 3;  // destination in the patch, float4 group of k
+    const int qi = (patch % a.npx) * kPatch + (ql % kPatch), qj = (patch / a.npx) * kPatch + (ql / kPatch);
     // the EM epilogue's operands, fetched before the view loop so their latency hides behind it
     const int k = kc0 + 4 * k4;
     const bool mine = qi < g.nx && qj < g.ny && k < g.nz;
@@ -143,42 +172,38 @@ __global__ void __launch_bounds__(kGT) k_adj_gather(const __grid_constant__ CUte
     }
 
     KSum acc[4];
+    bool failed = false;
     for (int v = 0; v < a.nv; ++v) {
         const int s = v % kStages;
-        const bool ok = mbar_wait_bounded(bar + s, (unsigned)(v / kStages) & 1u);
-        if (ok) {
-            const float* box = sm + (size_t)s * a.stage_floats;
-            const AdjEntry* e = reinterpret_cast<const AdjEntry*>(box + a.box_floats) + ql * MAXE;
-            AdjEntry en[MAXE];
+        if (!failed) {
+            if (mbar_wait_bounded(full + s, (unsigned)(v / kStages) & 1u)) {
+                const float* box = sm + (size_t)s * a.stage_floats;
+                const AdjEntry* e = reinterpret_cast<const AdjEntry*>(box + a.box_floats) + ql * MAXE;
+                AdjEntry en[MAXE];
 #pragma unroll
-            for (int m = 0; m < MAXE; ++m) en[m] = e[m];
-            float4 tv[MAXE];
+                for (int m = 0; m < MAXE; ++m) en[m] = e[m];
+                float4 tv[MAXE];
 #pragma unroll
-            for (int m = 0; m < MAXE; ++m) tv[m] = *reinterpret_cast<const float4*>(box + en[m].p + 4 * k4);
-            float sv[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int m = 0; m < MAXE; ++m) tv[m] = *reinterpret_cast<const float4*>(box + en[m].p + 4 * k4);
+                float sv[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int m = 0; m < MAXE; ++m) {
-                sv[0] = fmaf(en[m].w, tv[m].x, sv[0]);
-                sv[1] = fmaf(en[m].w, tv[m].y, sv[1]);
-                sv[2] = fmaf(en[m].w, tv[m].z, sv[2]);
-                sv[3] = fmaf(en[m].w, tv[m].w, sv[3]);
+                for (int m = 0; m < MAXE; ++m) {
+                    sv[0] = fmaf(en[m].w, tv[m].x, sv[0]);
+                    sv[1] = fmaf(en[m].w, tv[m].y, sv[1]);
+                    sv[2] = fmaf(en[m].w, tv[m].z, sv[2]);
+                    sv[3] = fmaf(en[m].w, tv[m].w, sv[3]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u].add(sv[u]);
+            } else {
+                failed = true;
+                *abort_flag = 1;
             }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) acc[u].add(sv[u]);
         }
-        if (__syncthreads_or(!ok)) {  // a copy never landed: give the ones in flight a last chance, then stop
-            if (tid == 0) {
-                if (err) atomicExch(err, (int)SPECT_ETIMEOUT);
-                for (int u = v; u < v + kStages && u < a.nv; ++u)
-                    mbar_wait_bounded(bar + (u % kStages), (unsigned)(u / kStages) & 1u);
-            }
-            return;
-        }
-            if (tid == 0 && v + kStages < a.nv) {  // stage s has been read by every thread
-            fence_proxy_async_smem();
-            issue(v + kStages);
-        }
+        // release the stage (also after a failed wait, so the producer never waits on it)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(empty + s)) : "memory");
     }
+    if (failed || *abort_flag) return;
 
     if (!mine) return;
     const float xv[4] = {ex.x, ex.y, ex.z, ex.w}, sv4[4] = {es.x, es.y, es.z, es.w}, uv[4] = {eu.x, eu.y, eu.z, eu.w};
@@ -197,7 +222,9 @@ int stage_floats(int box_floats, int ent_bytes) { return (box_floats + ent_bytes
 
 size_t gather_smem(int box_floats, int ent_bytes)
 {
-    return (size_t)kStages * stage_floats(box_floats, ent_bytes) * sizeof(float) + kStages * sizeof(uint64_t);
+    // stages | full and empty barriers | abort flag
+    return (size_t)kStages * stage_floats(box_floats, ent_bytes) * sizeof(float) + 2 * kStages * sizeof(uint64_t) +
+           16;
 }
 
 }  // namespace
@@ -316,7 +343,7 @@ cudaError_t launch_adj_gather(const spect_plan_s& P, int l0, int nv, float* out,
         cudaError_t e = cudaFuncSetAttribute(k_adj_gather<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                                              (int)smem);                                                     \
         if (e != cudaSuccess) return e;                                                                      \
-        k_adj_gather<M><<<grid, kGT, smem, st>>>(map, a, P.gboxes, P.gent, out, accumulate, em, P.err);      \
+        k_adj_gather<M><<<grid, kGT + 32, smem, st>>>(map, a, P.gboxes, P.gent, out, accumulate, em, P.err); \
         break;                                                                                               \
     }
         SPECT_G(1) SPECT_G(2) SPECT_G(3) SPECT_G(4) SPECT_G(5) SPECT_G(6) SPECT_G(7) SPECT_G(8)
