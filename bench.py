@@ -149,6 +149,19 @@ def algorithmic_flops(kind: str, nv: float, sep: bool, fused: bool = False) -> f
 NCU_TRAFFIC_BYTES_128 = {"conv_adj": 1161.4e6, "conv_fwd": 896.7e6, "rotate_atten": 1409.4e6, "rotate_adj": 1111.6e6}
 
 
+def aggregate_timing(total_ms: float, steps: int, world: int, dist=None, device="cpu"):
+    """Whole-job figures of a replicas run: every rank timed `steps` EM iterations of
+    its own reconstruction; the job's time is the slowest rank's (max over ranks)
+    and its throughput counts the pairs of all ranks.  Returns (total ms,
+    ms per step, pairs/s)."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, total_ms / steps, world * steps / (total_ms / 1e3)
+
+
 def peaks(torch, dev_index):
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     mp = json.load(open(path)) if os.path.exists(path) else {}
@@ -210,13 +223,9 @@ def run_ours(args):
         wall = time.perf_counter() - t0
     launches = plan.profile_read(reset=True)
     plan.check()
+    total_ms, ms_per_step, value = aggregate_timing(total_ms, args.steps, world, dist, device)
     if dist:
-        t = torch.tensor([total_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
-    ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
     n_launch = sum(v[0] for v in launches.values())
 
     # per-kernel device time on the launch stream (second pass, events around every launch)
