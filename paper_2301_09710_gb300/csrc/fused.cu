@@ -238,6 +238,8 @@ struct FusedDims {
     int nib, nkb;
     int TI, nT; // tile width in columns (multiple of CX), tiles per plane
     int wpf;    // row pitch of the untiled plane image (odd, >= nib*CX + 2*C)
+    int wz;     // row pitch of the adjoint's Zb (multiple of 4, wz/4 odd: conflict-free float4 windows)
+    int zarea;  // floats of Zb, nz x wz
     int farea;  // floats of the untiled plane image (the rotation kernel's shared memory)
     int urows;  // rows of U / ACC / MB per tile: min(TI, nx)
     int vrows;  // detector rows a tile's k-adjoint needs: min(nx, TI + 2*C)
@@ -259,7 +261,7 @@ __host__ __device__ inline size_t fwd_smem_floats(const FusedDims& d, int nz, in
 __host__ __device__ inline size_t adj_smem_floats(const FusedDims& d, int PT)
 {
     // Zb | V | MB x2 | taps J x (FX[3],FZ[3]) | 2 mbarriers
-    return (size_t)d.warea + (size_t)d.vrows * d.kpu + 2 * (size_t)d.marea + 6 * (size_t)PT * d.J + 8;
+    return (size_t)d.zarea + (size_t)d.vrows * d.kpu + 2 * (size_t)d.marea + 6 * (size_t)PT * d.J + 8;
 }
 
 template <int P>
@@ -667,7 +669,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
     extern __shared__ __align__(16) float sm[];
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     float* Zb = sm;
-    float* V = Zb + d.warea;
+    float* V = Zb + d.zarea;
     float* MB = V + (size_t)d.vrows * d.kpu;  // [2][marea]
     float* TAP = MB + 2 * (size_t)d.marea;    // [J][FX 3 classes | FZ 3 classes] x PT, every plane of the group
     uint64_t* bar = reinterpret_cast<uint64_t*>(TAP + 6 * PT * (size_t)d.J);
@@ -707,7 +709,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
 
     // stage the detector plane v(:,:,l) transposed, zero outside the detector
     for (int e = tid; e < d.vrows * d.kpu; e += T) V[e] = 0.f;
-    for (int e = tid; e < d.warea; e += T) Zb[e] = 0.f;
+    for (int e = tid; e < d.zarea; e += T) Zb[e] = 0.f;
     if (tid == 0) {
         mbar_init(bar, 1);
         mbar_init(bar + 1, 1);
@@ -755,11 +757,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
             float* zc = Zb + zoff + r;
             if (k0 + CZ <= nz && !last) {
 #pragma unroll
-                for (int c = 0; c < CZ; ++c) zc[(k0 + c) * d.wp] = o[c];
+                for (int c = 0; c < CZ; ++c) zc[(k0 + c) * d.wz] = o[c];
             } else {
 #pragma unroll
                 for (int c = 0; c < CZ; ++c)
-                    if (k0 + c < nz) zc[(k0 + c) * d.wp] = (last && c == cl) ? e_last : o[c];
+                    if (k0 + c < nz) zc[(k0 + c) * d.wz] = (last && c == cl) ? e_last : o[c];
             }
         }
         __syncthreads();
@@ -778,10 +780,18 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
             for (int it = tid; it < nz * nibt; it += T) {
                 const int ib = it / nz, k = it - ib * nz;
                 const int li = ib * CX;  // first column of this run, relative to the tile
-                const float* zr = Zb + k * d.wp + li;
-                float win[CX + P - 1];
+                const float* zr = Zb + k * d.wz + li;
+                // window of CX + P - 1 columns as float4 loads (rows 16-byte aligned, pitch/4 odd)
+                constexpr int WN4 = (CX + P - 1 + 3) / 4;
+                float win[4 * WN4];
 #pragma unroll
-                for (int m = 0; m < CX + P - 1; ++m) win[m] = zr[m];
+                for (int m4 = 0; m4 < WN4; ++m4) {
+                    const float4 t = reinterpret_cast<const float4*>(zr)[m4];
+                    win[4 * m4] = t.x;
+                    win[4 * m4 + 1] = t.y;
+                    win[4 * m4 + 2] = t.z;
+                    win[4 * m4 + 3] = t.w;
+                }
                 float o[CX];
                 fir<P, CX, 1, 0>(FX, win, o);
                 // first / last detector column: edge-class taps (replicate-padding folds)
@@ -1215,6 +1225,12 @@ FusedDims dims_for(const Geometry& g, int J, int tiles)
     d.warea = (g.nz * d.wp + 3) & ~3;
     d.parea = d.nT * d.warea;
     d.wpf = (d.nib * S::CX + 2 * S::C) | 1;
+    {
+        int q = (d.TI + 2 * S::C + 3) / 4;
+        if ((q & 1) == 0) ++q;
+        d.wz = 4 * q;
+        d.zarea = g.nz * d.wz;
+    }
     d.farea = (g.nz * d.wpf + 3) & ~3;
     int kpu = d.nkb * S::CZ + 2 * S::ZH;
     kpu = (kpu + 3) & ~3;
