@@ -201,8 +201,8 @@ cudaError_t launch_build_adjacency_fixed(const spect_plan_s& P, cudaStream_t st)
 // shared-memory image; k_fwd_sep_fused (one block per view and depth group)
 // streams those images in by TMA and blurs them.  Its shared memory:
 //   W   two plane buffers, nz rows x wp columns: W[k][C + i] with replicate
-//       halo columns; wp is odd so the i-pass windows (lanes over k) are
-//       bank-conflict free and every window load is an immediate offset.
+//       halo columns; wp is a multiple of 4 with wp/4 odd, so the i-pass
+//       windows (lanes over k) load as bank-conflict-free float4s.
 //   U   nx rows x kpu: i-pass output, U[i][ZH + k], with zero halo columns;
 //       kpu/4 is odd so the k-pass float4 windows (lanes over i) are
 //       bank-conflict free.  Replicate padding along k enters as folded edge
@@ -231,13 +231,13 @@ constexpr int kFusedThreads = 640;
 // each side, so every tile is blurred independently.  nT = 1 is the untiled
 // case (TI = nib*CX >= nx).
 struct FusedDims {
-    int wp;     // W row pitch of one tile image (odd, >= TI + 2*C)
+    int wp;     // W row pitch of one tile image (pitch4odd(TI + 2*C))
     int warea;  // floats of one tile image, nz x wp (multiple of 4, keeps U 16-byte aligned)
     int parea;  // floats of one plane's tile images in the slab, nT x warea
     int kpu;    // U row pitch (>= nkb*CZ + 2*ZH, multiple of 4, pitch/4 odd)
     int nib, nkb;
     int TI, nT; // tile width in columns (multiple of CX), tiles per plane
-    int wpf;    // row pitch of the untiled plane image (odd, >= nib*CX + 2*C)
+    int wpf;    // row pitch of the untiled plane image (pitch4odd(nib*CX + 2*C))
     int wz;     // row pitch of the adjoint's Zb (multiple of 4, wz/4 odd: conflict-free float4 windows)
     int zarea;  // floats of Zb, nz x wz
     int farea;  // floats of the untiled plane image (the rotation kernel's shared memory)
@@ -271,6 +271,22 @@ __device__ __forceinline__ void load_window_f4(const float* base, float (&win)[S
 #pragma unroll
     for (int m4 = 0; m4 < Sep<P>::WZ / 4; ++m4) {
         const float4 t = row[m4];
+        win[4 * m4] = t.x;
+        win[4 * m4 + 1] = t.y;
+        win[4 * m4 + 2] = t.z;
+        win[4 * m4 + 3] = t.w;
+    }
+}
+
+// A sliding window along a plane-image row (16-byte aligned, pitch4odd pitch):
+// N floats (a multiple of 4) as float4 loads; the FIRs read its first CX + P - 1.
+template <int N>
+__device__ __forceinline__ void load_row_f4(const float* row, float (&win)[N])
+{
+    static_assert(N % 4 == 0, "window length must be a multiple of 4");
+#pragma unroll
+    for (int m4 = 0; m4 < N / 4; ++m4) {
+        const float4 t = reinterpret_cast<const float4*>(row)[m4];
         win[4 * m4] = t.x;
         win[4 * m4 + 1] = t.y;
         win[4 * m4 + 2] = t.z;
@@ -312,7 +328,7 @@ __device__ __forceinline__ void flag_timeout(int* err)
 // are warp-uniform and every gather is a coalesced run along k (96 k per
 // pass, 30 independent loads per lane in flight).  The plane is
 // assembled in shared memory as the blur kernel wants it -- W[k][C+i] with
-// replicate halo columns and odd pitch -- and leaves with one TMA bulk store,
+// replicate halo columns and pitch4odd pitch -- and leaves with one TMA bulk store,
 // so the blur kernel can bring it back with one bulk load.  A plane cut into
 // column tiles leaves instead as nT tile images W_t[k][c] = W[k][t*TI + c],
 // c < TI + 2C, written with coalesced stores.
@@ -535,9 +551,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
             for (int it = tid; it < nz * nibt; it += T) {
                 const int li = ib * CX;  // first column of this run, relative to the tile
                 const float* wr = W + k * d.wp + li;
-                float win[CX + P - 1];
-#pragma unroll
-                for (int m = 0; m < CX + P - 1; ++m) win[m] = wr[m];
+                float win[4 * ((CX + P - 1 + 3) / 4)];
+                load_row_f4(wr, win);
                 float o[CX];
                 fir<P, CX, -1, P - 1>(FX, win, o);
                 float* ur = U + li * d.kpu + ZH + k;
@@ -781,17 +796,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
                 const int ib = it / nz, k = it - ib * nz;
                 const int li = ib * CX;  // first column of this run, relative to the tile
                 const float* zr = Zb + k * d.wz + li;
-                // window of CX + P - 1 columns as float4 loads (rows 16-byte aligned, pitch/4 odd)
-                constexpr int WN4 = (CX + P - 1 + 3) / 4;
-                float win[4 * WN4];
-#pragma unroll
-                for (int m4 = 0; m4 < WN4; ++m4) {
-                    const float4 t = reinterpret_cast<const float4*>(zr)[m4];
-                    win[4 * m4] = t.x;
-                    win[4 * m4 + 1] = t.y;
-                    win[4 * m4 + 2] = t.z;
-                    win[4 * m4 + 3] = t.w;
-                }
+                float win[4 * ((CX + P - 1 + 3) / 4)];
+                load_row_f4(zr, win);
                 float o[CX];
                 fir<P, CX, 1, 0>(FX, win, o);
                 // first / last detector column: edge-class taps (replicate-padding folds)
@@ -940,9 +946,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_dir_fused(Geometry g, 
             for (int c = 0; c < CX; ++c) o[c] = 0.f;
             for (int bb = 0; bb < P; ++bb) {
                 const float* wr = W + (ZH + k - bb + C) * d.wp + li;
-                float win[CX + P - 1];
-#pragma unroll
-                for (int m = 0; m < CX + P - 1; ++m) win[m] = wr[m];
+                float win[4 * ((CX + P - 1 + 3) / 4)];
+                load_row_f4(wr, win);
                 float ob[CX];
                 fir<P, CX, -1, P - 1>(TAP + bb * PT, win, ob);
 #pragma unroll
@@ -1044,9 +1049,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_dir_fused(Geometry g, 
                 for (int c = 0; c < CX; ++c) o[c] = 0.f;
                 for (int bb = 0; bb < P; ++bb) {
                     const float* vr = Vx + (ZH + k + bb - C) * d.wp + li;
-                    float win[CX + P - 1];
-#pragma unroll
-                    for (int m = 0; m < CX + P - 1; ++m) win[m] = vr[m];
+                    float win[4 * ((CX + P - 1 + 3) / 4)];
+                    load_row_f4(vr, win);
                     float ob[CX];
                     fir<P, CX, 1, 0>(TK + bb * PT, win, ob);
 #pragma unroll
@@ -1221,16 +1225,12 @@ FusedDims dims_for(const Geometry& g, int J, int tiles)
     d.urows = d.TI < g.nx ? d.TI : g.nx;
     d.vrows = d.TI + 2 * S::C < g.nx ? d.TI + 2 * S::C : g.nx;
     d.marea = (d.urows * g.nz + 3) & ~3;
-    d.wp = (d.TI + 2 * S::C) | 1;
+    d.wp = pitch4odd(d.TI + 2 * S::C);
     d.warea = (g.nz * d.wp + 3) & ~3;
     d.parea = d.nT * d.warea;
-    d.wpf = (d.nib * S::CX + 2 * S::C) | 1;
-    {
-        int q = (d.TI + 2 * S::C + 3) / 4;
-        if ((q & 1) == 0) ++q;
-        d.wz = 4 * q;
-        d.zarea = g.nz * d.wz;
-    }
+    d.wpf = pitch4odd(d.nib * S::CX + 2 * S::C);
+    d.wz = pitch4odd(d.TI + 2 * S::C);
+    d.zarea = g.nz * d.wz;
     d.farea = (g.nz * d.wpf + 3) & ~3;
     int kpu = d.nkb * S::CZ + 2 * S::ZH;
     kpu = (kpu + 3) & ~3;

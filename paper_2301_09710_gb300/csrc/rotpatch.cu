@@ -243,7 +243,7 @@ cudaError_t launch_rot_patch(const spect_plan_s& P, int l0, int nv, cudaStream_t
     const int C = (P.bucket - 1) / 2;
     const int nib = (g.nx + 15) / 16;
     a.C = C;
-    a.wp = (nib * 16 + 2 * C) | 1;
+    a.wp = pitch4odd(nib * 16 + 2 * C);  // as the fused kernels' untiled plane image
     a.parea = (g.nz * a.wp + 3) & ~3;
     a.wcols = nib * 16 + 2 * C;
     a.ts = P.ts;

@@ -304,6 +304,16 @@ __device__ __forceinline__ void tma_store_wait_read()
 
 __device__ __forceinline__ void tma_store_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+// Row pitch (floats) of the shared-memory plane images: at least n, a multiple of
+// 4 with pitch/4 odd, so rows are 16-byte aligned and float4 loads with lanes
+// over rows are bank-conflict free.
+__host__ __device__ inline int pitch4odd(int n)
+{
+    int q = (n + 3) / 4;
+    if ((q & 1) == 0) ++q;
+    return 4 * q;
+}
+
 // Tiled 3D tensor load (TMA) of the box at coordinates (c0, c1, c2) of `map`
 // into shared memory (128-byte aligned), completing on `bar`.
 __device__ __forceinline__ void tma_load_3d(void* dst_smem, const CUtensorMap* map, int c0, int c1, int c2,
