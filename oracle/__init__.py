@@ -271,3 +271,32 @@ def poisson_loglik(x, y, rbar, mu, psf, dy: float, angles, nthreads: int = 0) ->
     y = _f64(y)
     pos = y > 0
     return float(np.sum(y[pos] * np.log(ybar[pos])) - np.sum(ybar))
+
+
+def osem_subsets(nview: int, n_subsets: int) -> list:
+    """View indices of each ordered subset: subset m holds the views l = m (mod M),
+    interleaved over the orbit (the paper runs OSEM with 4 subsets and does not
+    say how they are formed; interleaving is the usual choice)."""
+    if not 1 <= n_subsets <= nview:
+        raise ValueError("need 1 <= n_subsets <= nview")
+    return [np.arange(m, nview, n_subsets) for m in range(n_subsets)]
+
+
+def osem_step(x, y, rbar, mu, psf, dy: float, angles, n_subsets: int, nthreads: int = 0) -> np.ndarray:
+    """One OSEM iteration (the EM update of Eqs. (7)-(8), beta = 0, applied in turn
+    to each ordered subset of views with that subset's projector and sensitivity):
+
+        x <- x * A_S'(y_S / (A_S x + rbar_S)) / A_S'1   for S = S_0, ..., S_{M-1}.
+
+    psf with one view row (nview_psf = 1) serves every subset; otherwise the
+    subset's rows are taken.  Guards as em_step.  With M = 1 this is em_step.
+    """
+    x = _f64(x)
+    y = _f64(y)
+    angles = np.asarray(angles, dtype=np.float64)
+    psf = _f64(psf)
+    for idx in osem_subsets(len(angles), n_subsets):
+        p = psf if psf.shape[0] == 1 else psf[idx]
+        r = None if rbar is None else _f64(rbar)[idx]
+        x = em_step(x, y[idx], r, mu, p, dy, angles[idx], nthreads=nthreads)
+    return x

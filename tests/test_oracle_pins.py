@@ -376,3 +376,52 @@ def test_em_reg_solves_the_surrogate_quadratic():
     # and large beta pulls the update towards u
     xb = oracle.em_step_reg(xk, y, rbar, u, 1e9, prob.mu, psf, prob.dy, ang, s=s)
     np.testing.assert_allclose(xb, u, rtol=1e-5)
+
+
+# ------------------------------------------------------------------ OSEM (ordered subsets of views)
+def test_osem_subsets_partition_the_views():
+    subs = oracle.osem_subsets(12, 4)
+    allv = np.sort(np.concatenate(subs))
+    np.testing.assert_array_equal(allv, np.arange(12))
+    assert [list(s) for s in subs] == [[0, 4, 8], [1, 5, 9], [2, 6, 10], [3, 7, 11]]
+
+
+def test_osem_with_one_subset_is_mlem():
+    prob, psf, ang = _em_problem()
+    rng = np.random.default_rng(41)
+    y = rng.poisson(5.0, (prob.nview, 6, 16)).astype(np.float64)
+    rbar = np.full_like(y, 0.3)
+    x = np.ones((6, 16, 16))
+    np.testing.assert_array_equal(oracle.osem_step(x, y, rbar, prob.mu, psf, prob.dy, ang, 1),
+                                  oracle.em_step(x, y, rbar, prob.mu, psf, prob.dy, ang))
+
+
+def test_osem_last_subset_preserves_its_counts():
+    # with rbar = 0 each sub-iteration satisfies sum_j (A_S'1)_j x_j = sum_{i in S} y_i
+    prob, psf, ang = _em_problem()
+    y = np.random.default_rng(42).poisson(5.0, (prob.nview, 6, 16)).astype(np.float64)
+    x = oracle.osem_step(np.ones((6, 16, 16)), y, None, prob.mu, psf, prob.dy, ang, 3)
+    last = oracle.osem_subsets(prob.nview, 3)[-1]
+    s_last = oracle.sensitivity(prob.mu, psf, prob.dy, ang[last])
+    assert abs(np.sum(s_last * x) - y[last].sum()) <= 1e-11 * y[last].sum()
+    assert np.all(x >= 0)
+
+
+def test_osem_fixed_point_at_truth():
+    prob, psf, ang = _em_problem()
+    xt = prob.x.astype(np.float64) + 0.1
+    y = oracle.forward(xt, prob.mu, psf, prob.dy, ang)
+    np.testing.assert_allclose(oracle.osem_step(xt, y, None, prob.mu, psf, prob.dy, ang, 4), xt, rtol=1e-12)
+
+
+def test_osem_iteration_advances_further_than_mlem():
+    # the reason for subsets: one pass over M subsets makes about M updates' progress
+    prob, psf, ang = _em_problem()
+    xt = prob.x.astype(np.float64)
+    ybar = oracle.forward(xt, prob.mu, psf, prob.dy, ang) * 20
+    y = np.random.default_rng(43).poisson(ybar).astype(np.float64)
+    x0 = np.full_like(xt, xt.mean())
+    ll = lambda x: oracle.poisson_loglik(x, y, None, prob.mu, psf, prob.dy, ang)
+    x_em = oracle.em_step(x0, y, None, prob.mu, psf, prob.dy, ang)
+    x_os = oracle.osem_step(x0, y, None, prob.mu, psf, prob.dy, ang, 4)
+    assert ll(x_os) > ll(x_em) > ll(x0)
