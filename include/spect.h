@@ -253,6 +253,17 @@ spect_status spect_plan_check(spect_plan plan);
  */
 spect_status spect_plan_check_stream(spect_plan plan, spect_stream stream);
 
+/*
+ * spect_plan_selftest_timeout -- exercise the failure path of the bounded
+ * device waits without any fault: one thread waits, with the bounded mbarrier
+ * wait the fused kernels use on their bulk copies but a limit of spin_clocks
+ * SM clocks (0 .. 2^31), on a barrier that nothing completes; the wait runs out
+ * and SPECT_ETIMEOUT is recorded in the plan's error word, which the next
+ * spect_plan_check reports (and clears).  The plan stays usable.  A test aid
+ * (the paper has no counterpart).  Errors: SPECT_EINVAL, SPECT_ECUDA.
+ */
+spect_status spect_plan_selftest_timeout(spect_plan plan, long long spin_clocks, spect_stream stream);
+
 /* spect_plan_destroy -- release the plan; NULL is accepted and returns OK.
  * Waits for the plan's outstanding work on the device before freeing. */
 spect_status spect_plan_destroy(spect_plan plan);

@@ -98,6 +98,8 @@ def load(path: str = LIB_PATH):
         lib.spect_batch_destroy.restype = st
         lib.spect_plan_bytes.argtypes = [i, i, i, i, i, i, i, i, ctypes.c_uint, ctypes.POINTER(ctypes.c_size_t)]
         lib.spect_plan_bytes.restype = st
+        lib.spect_plan_selftest_timeout.argtypes = [vp, ctypes.c_longlong, vp]
+        lib.spect_plan_selftest_timeout.restype = st
         lib.spect_plan_check_stream.argtypes = [vp, vp]
         lib.spect_plan_check_stream.restype = st
         lib.spect_plan_destroy.argtypes = [vp]

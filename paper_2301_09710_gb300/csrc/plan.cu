@@ -759,6 +759,39 @@ spect_status em_iterate(spect_plan_s* P, float* x, const float* y, const float* 
 
 extern "C" {
 
+}  // extern "C"
+
+namespace {
+
+// One thread waits, with the bounded mbarrier wait of the fused kernels but a
+// limit of `spin_clocks`, on a barrier that nothing ever completes; the wait
+// runs out and the block records SPECT_ETIMEOUT in the error word, exactly as a
+// fused kernel whose bulk copy never landed would.
+__global__ void k_wait_selftest(int* err, long long spin_clocks)
+{
+    __shared__ __align__(8) uint64_t bar;
+    spect::mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    bool done = spect::mbar_try_wait(&bar, 0u);
+    const long long t0 = clock64();
+    while (!done && clock64() - t0 < spin_clocks) done = spect::mbar_try_wait(&bar, 0u);
+    if (!done && err) atomicExch(err, (int)SPECT_ETIMEOUT);
+}
+
+}  // namespace
+
+extern "C" {
+
+spect_status spect_plan_selftest_timeout(spect_plan P, long long spin_clocks, spect_stream stream)
+{
+    if (!P) return fail(SPECT_EINVAL, "plan is NULL");
+    if (spin_clocks < 0 || spin_clocks > (1ll << 31)) return fail(SPECT_EINVAL, "spin_clocks must be in [0, 2^31]");
+    k_wait_selftest<<<1, 1, 0, (cudaStream_t)stream>>>(P->err, spin_clocks);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(SPECT_ECUDA, std::string("self-test launch: ") + cudaGetErrorString(e));
+    return SPECT_OK;
+}
+
 spect_status spect_plan_check_stream(spect_plan P, spect_stream stream)
 {
     if (!P) return fail(SPECT_EINVAL, "plan is NULL");

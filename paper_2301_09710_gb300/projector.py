@@ -193,6 +193,11 @@ class SpectPlan:
         else:
             _lib.check(self.lib.spect_plan_check(self.handle))
 
+    def selftest_timeout(self, spin_clocks: int = 1 << 22, stream=None) -> None:
+        """Make one bounded device wait run out (nothing completes it): the next
+        check() raises SpectError(SPECT_ETIMEOUT); the plan stays usable."""
+        _lib.check(self.lib.spect_plan_selftest_timeout(self.handle, int(spin_clocks), _stream_handle(stream)))
+
     def profile(self, enable: bool = True) -> None:
         """Bracket every later kernel launch with CUDA events on its stream."""
         _lib.check(self.lib.spect_profile_enable(self.handle, int(bool(enable))))
