@@ -258,29 +258,72 @@ def run_ours(args):
                 "probe_tflops": probe,
                 "kernels": kern}
 
-    # end to end through the public API: host (pinned) buffers, copies inside the timed region
+    # end to end through the public API: every step copies its inputs (x, y, rbar) from pinned host memory and
+    # reads its result back, all inside one timed region; the copies run on two copy streams, double-buffered,
+    # so step k+1's uploads and step k's download overlap the EM steps (as a serving loop would run them).
+    # Every step moves more than L2 (plane slabs, attenuation cache), so no flush is needed between steps.
     xh = torch.from_numpy(x0_h).pin_memory()
     yh = torch.from_numpy(y_h).pin_memory()
     rh = torch.from_numpy(rbar_h).pin_memory()
-    xo = torch.empty_like(xh).pin_memory()
-    xd, yd, rd = torch.empty_like(x), torch.empty_like(y), torch.empty_like(rbar)
+    xo = [torch.empty_like(xh).pin_memory() for _ in range(2)]
+    bufs = [(torch.empty_like(x), torch.empty_like(y), torch.empty_like(rbar)) for _ in range(2)]
+    up, down = torch.cuda.Stream(device=device), torch.cuda.Stream(device=device)
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_step = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+
+    def upload(b):
+        with torch.cuda.stream(up):
+            up.wait_event(ev_out[b])  # buffer b's previous step and download are done
+            for d_, h_ in zip(bufs[b], (xh, yh, rh)):
+                d_.copy_(h_, non_blocking=True)
+            ev_in[b].record(up)
+
+    def e2e_run(k):
+        for e in ev_out:
+            e.record(down)
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        up.wait_event(a)
+        upload(0)
+        for s_ in range(k):
+            b = s_ % 2
+            stream.wait_event(ev_in[b])
+            plan.em_step(bufs[b][0], bufs[b][1], bufs[b][2], niter=1)
+            ev_step[b].record(stream)
+            if s_ + 1 < k:
+                upload(1 - b)
+            with torch.cuda.stream(down):
+                down.wait_event(ev_step[b])
+                xo[b].copy_(bufs[b][0], non_blocking=True)
+                ev_out[b].record(down)
+        stream.wait_event(ev_out[(k - 1) % 2])
+        z.record(stream)
+        z.synchronize()
+        return a.elapsed_time(z)
+
+    e2e_run(2)  # warm-up of the streams and pinned buffers
+    e_ms = e2e_run(args.steps)
+    # the same steps with nothing overlapped (copy in, EM step, copy out, one after the other), for reference
+    xd, yd, rd = bufs[0]
     torch.cuda.synchronize()
-    e_ms = 0.0
+    s_ms = 0.0
     for _ in range(args.steps):
-        flush.fill_(1.0)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         xd.copy_(xh, non_blocking=True)
         yd.copy_(yh, non_blocking=True)
         rd.copy_(rh, non_blocking=True)
         plan.em_step(xd, yd, rd, niter=1)
-        xo.copy_(xd, non_blocking=True)
-        b.record(stream)
-        b.synchronize()
-        e_ms += a.elapsed_time(b)
+        xo[0].copy_(xd, non_blocking=True)
+        z.record(stream)
+        z.synchronize()
+        s_ms += a.elapsed_time(z)
     e2e = {"value": world * args.steps / (e_ms / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": int(xh.numel() * 4 + yh.numel() * 4 + rh.numel() * 4),
-           "d2h_bytes_per_step": int(xo.numel() * 4)}
+           "d2h_bytes_per_step": int(xo[0].numel() * 4),
+           "copies": "pinned host buffers; uploads of step k+1 and download of step k overlap the EM steps",
+           "serial_value": world * args.steps / (s_ms / 1e3)}
 
     direct = None
     if args.direct_steps > 0 and args.path == "separable":
