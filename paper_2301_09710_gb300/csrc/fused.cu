@@ -10,12 +10,15 @@
 //  * The Eq. (1) attenuation factor mubar is computed once per plan for every
 //    view, [l][j][i][k] (nview * nx*ny*nz floats; HBM is plentiful), so the hot
 //    kernels multiply by a streamed, coalesced value instead of re-rotating mu.
-//  * Forward: one block per (view, group of J depth planes).  Per plane it
-//    rotates and attenuates the whole (i,k) plane into shared memory, runs the
-//    separable PSF blur as two register-blocked sliding-window passes (i, then
-//    k, replicate padding materialised as halo rows/columns), and accumulates
-//    the plane into register partial sums; the groups' partials are added in
-//    a fixed order by a small reduce kernel (deterministic, no atomics).
+//  * Forward: a rotation kernel rotates and attenuates every (view, depth)
+//    plane into the work slab, already laid out as the blur kernel's shared-
+//    memory image (replicate halo columns, conflict-free pitch).  The blur
+//    kernel (one block per view and group of J depth planes) streams those
+//    images in by TMA, runs the separable PSF blur as two register-blocked
+//    sliding-window passes (i, then k; replicate padding along k folded into
+//    edge taps), and accumulates the group's depth sum in shared memory; the
+//    groups' partials are added in a fixed order by a small reduce kernel
+//    (deterministic, no atomics).
 //  * Transpose: one block per (view, depth group) expands the detector plane
 //    into blurred-adjoint planes times mubar (the t slab, [v][j][i][k]); a
 //    gather kernel then sums sum_l sum_p W_l(p;q) t_l(p,k) per destination voxel
@@ -348,7 +351,8 @@ __global__ void __launch_bounds__(kRotThreads, 2) k_rot_fwd(Geometry g, FusedDim
     constexpr int C = Sep<P>::C;
     extern __shared__ __align__(16) float sm[];
     float* S = sm;
-    float* MU = sm + d.farea;  // [i][k] attenuation plane (MUS)
+    float* TBL = sm + d.farea;  // the (view, row) rotation table: nx float4 weights, then nx bases
+    float* MU = TBL + d.ts;     // [i][k] attenuation plane (MUS)
     uint64_t* bar = reinterpret_cast<uint64_t*>(MU + d.ps);
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -358,25 +362,26 @@ __global__ void __launch_bounds__(kRotThreads, 2) k_rot_fwd(Geometry g, FusedDim
     const int wp = d.wpf;
     const int wcols = d.nib * Sep<P>::CX + 2 * C;
     const float* tab = rtab + ((size_t)l * ny + j) * d.ts;
-    const float4* TW = reinterpret_cast<const float4*>(tab);
-    const int* TB = reinterpret_cast<const int*>(tab + 4 * nx);
     const float* mb = mubar + ((size_t)l * ny + j) * d.ps;
-    if (MUS) {
-        if (threadIdx.x == 0) {
-            mbar_init(bar, 1);
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            tma_load_1d(MU, mb, (unsigned)d.ps * 4u, bar);
-        }
-        __syncthreads();  // the barrier is initialised before anyone waits on it
+    if (MUS && threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tma_load_1d(MU, mb, (unsigned)d.ps * 4u, bar);
     }
+    // the table is staged once, so no row step waits on a table load before its gathers
+    for (int e = threadIdx.x; e < d.ts / 4; e += kRotThreads)
+        reinterpret_cast<float4*>(TBL)[e] = __ldg(reinterpret_cast<const float4*>(tab) + e);
+    __syncthreads();  // table staged; the barrier is initialised before anyone waits on it
+    const float4* TW = reinterpret_cast<const float4*>(TBL);
+    const int* TB = reinterpret_cast<const int*>(TBL + 4 * nx);
     bool ok = true, waited = !MUS;
 
     for (int i = 2 * warp; i < nx; i += 2 * NW) {
         const bool two = i + 1 < nx;
-        const float4 wa = __ldg(TW + i);
-        const float4 wb = two ? __ldg(TW + i + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float* pa = xt + (size_t)__ldg(TB + i) * nz;
-        const float* pb = xt + (size_t)__ldg(TB + (two ? i + 1 : i)) * nz;
+        const float4 wa = TW[i];
+        const float4 wb = two ? TW[i + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float* pa = xt + (size_t)TB[i] * nz;
+        const float* pb = xt + (size_t)TB[two ? i + 1 : i] * nz;
         for (int k0 = 0; k0 < nz; k0 += 96) {
             float xa[3][4], xb[3][4], ma[3], mc[3];
 #pragma unroll
@@ -446,7 +451,7 @@ __global__ void __launch_bounds__(kRotThreads, 2) k_rot_fwd(Geometry g, FusedDim
         if (threadIdx.x == 0) {
             fence_proxy_async_smem();
             tma_store_1d(dst, S, (unsigned)d.parea * 4u);
-            tma_store_wait_all();
+            tma_store_wait_read<0>();  // the block may leave once its shared memory is read
         }
         return;
     }
@@ -738,7 +743,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
     }
     __syncthreads();
 
-    unsigned phase[2] = {0u, 0u};
+    unsigned phases = 0u;  // bit b: parity of buffer b's barrier
     for (int j = j_begin; j < j_end; ++j) {
         const int n = j - j_begin, b = n & 1;
         const float* FX = TAP + n * 6 * PT;
@@ -789,8 +794,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
 
         // i-adjoint times mubar, in place in MB[b]; lanes over k
         float* mb = MB + b * (size_t)d.marea;
-        const bool ok = mbar_wait_bounded(bar + b, phase[b]);
-        phase[b] ^= 1u;
+        const bool ok = mbar_wait_bounded(bar + b, (phases >> b) & 1u);
+        phases ^= 1u << b;
         if (ok) {
             for (int it = tid; it < nz * nibt; it += T) {
                 const int ib = it / nz, k = it - ib * nz;
@@ -829,7 +834,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 flag_timeout(err);
-                mbar_wait_bounded(bar + b, phase[b] ^ 1u);
+                mbar_wait_bounded(bar + b, ((phases >> b) & 1u) ^ 1u);
                 tma_store_wait_all();
             }
             return;
@@ -840,7 +845,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
             tma_store_1d(tsl + (size_t)j * d.ps, mb, SPECT_MBYTES);
         }
     }
-    if (tid == 0) tma_store_wait_all();
+    if (tid == 0) tma_store_wait_read<0>();  // the writes complete with the grid
 #undef SPECT_MBYTES
 }
 
@@ -1062,6 +1067,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_dir_fused(Geometry g, 
                     auto edge = [&](int c, int ci) {
                         const float* TC = TAP + (size_t)(ci * cls_z + ck) * P * PT;
                         float acc = 0.f;
+#pragma unroll 2
                         for (int bb = 0; bb < P; ++bb) {
                             const float* vr = Vx + (ZH + k + bb - C) * d.wp + li + c;
                             float rp = 0.f;
@@ -1097,7 +1103,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_dir_fused(Geometry g, 
             tma_store_1d(tsl + (size_t)j * d.ps, mb, mbytes);
         }
     }
-    if (tid == 0) tma_store_wait_all();
+    if (tid == 0) tma_store_wait_read<0>();  // the writes complete with the grid
 }
 
 // x_t(q,k) (+)= sum_{v in chunk} sum_{e < MAXE} w_e t[v][p_e][k]
@@ -1244,6 +1250,9 @@ FusedDims dims_for(const Geometry& g, int J, int tiles)
     return d;
 }
 
+// Rotation kernel without the attenuation plane staged: plane image + table.
+inline size_t rot_smem_min(const FusedDims& d) { return ((size_t)d.farea + d.ts) * sizeof(float); }
+
 template <int P>
 size_t smem_fwd(const Geometry& g, const FusedDims& d)
 {
@@ -1269,7 +1278,7 @@ int tiles_that_fit(const Geometry& g, size_t limit, int min_tiles)
         const FusedDims d = dims_for<P>(g, 8, t);
         if (d.nT == last_nt) continue;  // same tile width as a smaller request
         last_nt = d.nT;
-        if (smem_fwd<P>(g, d) <= limit && smem_adj<P>(g, d) <= limit && (size_t)d.farea * 4 <= limit &&
+        if (smem_fwd<P>(g, d) <= limit && smem_adj<P>(g, d) <= limit && rot_smem_min(d) <= limit &&
             (size_t)d.marea * 4 < (1u << 20))
             return d.nT;
     }
@@ -1292,9 +1301,9 @@ template <int P>
 cudaError_t rot_launch(const spect_plan_s& Pl, const float* xt, int l0, int nv, cudaStream_t st)
 {
     const FusedDims d = dims_for<P>(Pl.g, Pl.fused_J, Pl.fused_nT);
-    const size_t smem_mu = ((size_t)d.farea + d.ps) * sizeof(float) + 16;
+    const size_t smem_mu = rot_smem_min(d) + (size_t)d.ps * sizeof(float) + 16;
     const bool mus = smem_mu <= (size_t)Pl.smem_optin;
-    const size_t smem = mus ? smem_mu : (size_t)d.farea * sizeof(float);
+    const size_t smem = mus ? smem_mu : rot_smem_min(d);
     auto kern = mus ? k_rot_fwd<P, true> : k_rot_fwd<P, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1335,7 +1344,7 @@ bool dir_fits(const Geometry& g, size_t limit, int J, int adj_J)
     const int cls_z = g.nz >= 2 ? 3 : 1;
     const FusedDims df = dims_for<P>(g, J, 1), da = dims_for<P>(g, adj_J, 1);
     return df.nT == 1 && dir_smem_fwd<P>(g, df) <= limit && dir_smem_adj<P>(g, da, cls_z) <= limit &&
-           (size_t)df.farea * 4 <= limit && (size_t)df.ps * 4 < (1u << 20);
+           rot_smem_min(df) <= limit && (size_t)df.ps * 4 < (1u << 20);
 }
 
 template <int P>
@@ -1416,7 +1425,7 @@ int fused_tiles_fit(const Geometry& g, int bucket, int J, int adj_J, int tiles, 
         constexpr int B = decltype(tag)::value;
         const FusedDims df = dims_for<B>(g, J, tiles), da = dims_for<B>(g, adj_J, tiles);
         const bool ok = smem_fwd<B>(g, df) <= smem_limit && smem_adj<B>(g, da) <= smem_limit &&
-                        (size_t)df.farea * 4 <= smem_limit && (size_t)df.marea * 4 < (1u << 20);
+                        rot_smem_min(df) <= smem_limit && (size_t)df.marea * 4 < (1u << 20);
         return ok ? df.nT : 0;
     };
     switch (bucket) {
