@@ -146,7 +146,7 @@ def algorithmic_flops(kind: str, nv: float, sep: bool, fused: bool = False) -> f
 
 # DRAM bytes (read + write) per 128-view launch of the fused separable kernels, from one ncu capture of the
 # 32-view case scaled by 4 (profiles/fused_kernels_128x128x80_32views.md); valid for the kernels as captured.
-NCU_TRAFFIC_BYTES_128 = {"conv_adj": 1164.0e6, "conv_fwd": 891.9e6, "rotate_atten": 1404.6e6, "rotate_adj": 1109.2e6}
+NCU_TRAFFIC_BYTES_128 = {"conv_adj": 1156.6e6, "conv_fwd": 890.8e6, "rotate_atten": 1402.9e6, "rotate_adj": 1108.6e6}
 
 
 def aggregate_timing(total_ms: float, steps: int, world: int, dist=None, device="cpu"):

@@ -319,6 +319,43 @@ __device__ __forceinline__ void fir(const float* taps, const float (&win)[WN], f
     }
 }
 
+// sum_b taps[b] w[b + SH] for b = 0..P-1, in that order (one FMA chain)
+template <int P, int SH, int N>
+__device__ __forceinline__ float tap_dot(const float* taps, const float (&w)[N])
+{
+    constexpr int PT = Sep<P>::PT;
+    static_assert(P - 1 + SH < N, "window too short");
+    float s = 0.f;
+#pragma unroll
+    for (int b4 = 0; b4 < PT / 4; ++b4) {
+        const float4 f4 = reinterpret_cast<const float4*>(taps)[b4];
+        const float fv[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (4 * b4 + u < P) s = fmaf(fv[u], w[4 * b4 + u + SH], s);
+    }
+    return s;
+}
+
+// sum_b taps[b] row[s + b] for b = 0..P-1 (the edge-class output of an adjoint
+// FIR): the samples come in as float4 loads from the aligned position s & ~3
+// (row 16-byte aligned, pitch4odd pitch: conflict-free with lanes over rows)
+// and the shift s & 3 selects a compile-time offset, so no lane issues P
+// dependent scalar loads.  The loads may read up to 3 floats past row[s + P - 1]
+// (still inside the caller's shared memory); those are never used.
+template <int P>
+__device__ __forceinline__ float edge_tap_dot(const float* taps, const float* row, int s)
+{
+    float w[4 * ((P + 3 + 3) / 4)];
+    load_row_f4(row + (s & ~3), w);
+    switch (s & 3) {
+        case 0: return tap_dot<P, 0>(taps, w);
+        case 1: return tap_dot<P, 1>(taps, w);
+        case 2: return tap_dot<P, 2>(taps, w);
+        default: return tap_dot<P, 3>(taps, w);
+    }
+}
+
 // Record a timed-out bounded wait in the plan's error word.
 __device__ __forceinline__ void flag_timeout(int* err)
 {
@@ -420,16 +457,22 @@ __global__ void __launch_bounds__(kRotThreads, 2) k_rot_fwd(Geometry g, FusedDim
                     va = fmaf(wa.z, xa[q][2], va);
                     va = fmaf(wa.w, xa[q][3], va);
                     va *= ma[q];
-                    wr[i] = va;
                     if (two) {
                         float vb = wb.x * xb[q][0];
                         vb = fmaf(wb.y, xb[q][1], vb);
                         vb = fmaf(wb.z, xb[q][2], vb);
                         vb = fmaf(wb.w, xb[q][3], vb);
                         vb *= mc[q];
-                        wr[i + 1] = vb;
+                        if (C % 2 == 0) {  // i even: one 8-byte store (half the bank conflicts of two)
+                            *reinterpret_cast<float2*>(wr + i) = make_float2(va, vb);
+                        } else {
+                            wr[i] = va;
+                            wr[i + 1] = vb;
+                        }
                         if (i + 1 == nx - 1)
                             for (int h = nx; h < wcols - C; ++h) wr[h] = vb;
+                    } else {
+                        wr[i] = va;
                     }
                     if (i == 0)  // replicate padding along i: left halo columns
                         for (int h = -C; h < 0; ++h) wr[h] = va;
@@ -768,12 +811,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
             }
             const int cl = nz - 1 - k0;  // position of row k = nz-1 in this block
             const bool last = nz > 1 && cl < CZ;
-            float e_last = 0.f;
-            if (last) {
-                const float* f = FZ + 2 * PT;
-                const float* vv = vr + (nz - 1) - C + ZH;
-                for (int bb = 0; bb < P; ++bb) e_last = fmaf(f[bb], vv[bb], e_last);
-            }
+            const float e_last = last ? edge_tap_dot<P>(FZ + 2 * PT, vr, (nz - 1) - C + ZH) : 0.f;
             float* zc = Zb + zoff + r;
             if (k0 + CZ <= nz && !last) {
 #pragma unroll
@@ -815,11 +853,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
                 }
                 const int cl = last_col - li;  // position of column nx-1 in this run
                 const bool last = cl < CX;
-                float e_last = 0.f;
-                if (last) {
-                    const float* f = FX + 2 * PT;
-                    for (int a = 0; a < P; ++a) e_last = fmaf(f[a], zr[cl + a], e_last);
-                }
+                const float e_last = last ? edge_tap_dot<P>(FX + 2 * PT, zr - li, li + cl) : 0.f;
                 float* mp = mb + li * nz + k;
                 if (!last) {
 #pragma unroll
