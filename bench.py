@@ -128,19 +128,20 @@ def make_workload(device, path, nview=NVIEW, autotune=True):
     return prob, plan, x0, y, rbar
 
 
-def algorithmic_flops(kind: str, nv: float, sep: bool, fused: bool = False) -> float:  # noqa: C901
+def algorithmic_flops(kind: str, nv: float, sep: bool, fused: bool = False) -> float:
     """Algorithmic FLOPs of one launch of a kernel class that processes nv views.
 
     Per voxel-view: blur 2(px+pz) (separable) or 2 px pz (full PSF); bilinear
     rotation 7 (4 mul + 3 add); attenuation multiply 1; depth or view sum 1;
-    adjoint rotation 8 (4 weighted adds).  The fused forward kernel also
-    rotates and attenuates (7 + 1 + 1 on top of the blur); the low-memory
-    rotate kernel also rebuilds the attenuation (~20 in all).
+    adjoint rotation 8 (4 weighted adds).  The fused path's rotation kernel
+    rotates and attenuates (7 + 1) and its blur kernel blurs and sums over
+    depth; the low-memory rotate kernel also rebuilds the attenuation (~20 in
+    all).
     """
     vv = float(NX) * NX * NZ * nv  # voxel-views
     conv = 2.0 * (PSF + PSF) if sep else 2.0 * PSF * PSF
-    per = {"conv_fwd": conv + (9.0 if fused else 1.0), "conv_adj": conv + 1.0,
-           "rotate_atten": 20.0, "rotate_adj": 8.0}.get(kind, 0.0)
+    per = {"conv_fwd": conv + 1.0, "conv_adj": conv + 1.0,
+           "rotate_atten": 8.0 if fused else 20.0, "rotate_adj": 8.0}.get(kind, 0.0)
     return per * vv
 
 
