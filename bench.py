@@ -36,7 +36,8 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)  # about 0.6 s timed: several clock samples
+    # default: 1000 GPU steps (about 1.9 s timed, several clock samples); 3 oracle steps for --impl reference
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--path", choices=["separable", "direct"], default="separable")
@@ -46,7 +47,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default launch shapes")
     ap.add_argument("--nview", type=int, default=NVIEW,
                     help="views of the workload (default 128; fewer only for small profiler captures)")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.steps is None:
+        a.steps = 3 if a.impl == "reference" else 1000
+    return a
 
 
 # ---------------------------------------------------------------- clocks sampler
@@ -69,6 +73,14 @@ class Clocks:
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+        # nvidia-smi takes a moment to start: wait (at most 3 s) for its first sample, so the samples fall
+        # inside the timed region that follows
+        t0 = time.perf_counter()
+        while self.proc is not None and self.proc.poll() is None and time.perf_counter() - t0 < 3.0:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
+        self.skip = 1 if self.path and os.path.exists(self.path) and os.path.getsize(self.path) > 0 else 0
         return self
 
     def __exit__(self, *exc):
@@ -85,7 +97,8 @@ class Clocks:
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
-            for line in f:
+            lines = f.readlines()[getattr(self, "skip", 0):]  # the first sample precedes the timed region
+            for line in lines:
                 parts = [p.strip() for p in line.split(",")]
                 if len(parts) < 9:
                     continue
@@ -401,6 +414,9 @@ def cpu_name():
     return os.uname().machine
 
 
+REF_BUDGET_S = 150.0  # timed oracle work of one --impl reference run, at most
+
+
 def run_reference(args):
     """The oracle as it stands on the host cores, each step a bounded view sample."""
     rank = int(os.environ.get("RANK", "0"))
@@ -422,14 +438,22 @@ def run_reference(args):
     rbar = synthetic.background_from(v.astype(np.float32), 0.1, 8.0)
     for _ in range(args.warmup if args.warmup < 1 else 1):
         x = oracle.em_step(x, y, rbar, prob.mu, psf, prob.dy, ang, s=s, nthreads=nth)
+    # the oracle takes seconds per step: a run asked for many steps stops once REF_BUDGET_S of timed work is
+    # done (the rate is per step, so it does not depend on how many were taken) and reports the count it timed
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    done = 0
+    while done < args.steps:
         x = oracle.em_step(x, y, rbar, prob.mu, psf, prob.dy, ang, s=s, nthreads=nth)
+        done += 1
+        el = time.perf_counter() - t0
+        if el + el / done > REF_BUDGET_S:
+            break
     dt = time.perf_counter() - t0
-    value = args.steps * (nsub / NVIEW) / dt
+    value = done * (nsub / NVIEW) / dt
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3 * NVIEW / nsub, "higher_is_better": True,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": done,
+        "steps_requested": args.steps, "warmup": args.warmup, "ms_per_step": dt / done * 1e3 * NVIEW / nsub,
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "128x128x80 image, 128 views, 37x37 PSF, MLEM step (oracle on a view sample)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": nth,
