@@ -31,6 +31,8 @@ def test_config2_sampled_views(prob, path):
     ang = oracle.default_angles(128)
     plan = make_plan(prob, ang, path)
     assert plan.info()["fused"] == (path in ("fused", "direct"))
+    if plan.info()["fused"]:
+        plan.autotune()  # the launch shapes the benchmark times
     x = dev(prob.x)
     v = host(plan.forward(x))
     psf = oracle_psf(prob, path)
