@@ -61,11 +61,13 @@ def _load():
             d = ctypes.c_double
             lib.oracle_rotate_slice.argtypes = [i, d, dp, dp]
             lib.oracle_rotate_adjoint_slice.argtypes = [i, d, dp, dp]
+            lib.oracle_rotate3_slice.argtypes = [i, d, dp, dp]
+            lib.oracle_rotate3_adjoint_slice.argtypes = [i, d, dp, dp]
             lib.oracle_attenuation.argtypes = [i, i, i, d, dp, dp]
             lib.oracle_conv_plane.argtypes = [i, i, dp, dp, i, i, dp]
             lib.oracle_conv_adjoint_plane.argtypes = [i, i, dp, dp, i, i, dp]
-            lib.oracle_forward.argtypes = [i, i, i, i, dp, dp, d, dp, i, i, i, dp, dp, i]
-            lib.oracle_back.argtypes = [i, i, i, i, dp, dp, d, dp, i, i, i, dp, dp, i]
+            lib.oracle_forward.argtypes = [i, i, i, i, dp, dp, d, dp, i, i, i, dp, dp, i, i]
+            lib.oracle_back.argtypes = [i, i, i, i, dp, dp, d, dp, i, i, i, dp, dp, i, i]
             lib.oracle_max_threads.restype = i
             _lib = lib
     return _lib
@@ -106,6 +108,29 @@ def rotate_adjoint_slice(img2d, theta: float) -> np.ndarray:
     out = np.empty_like(a)
     _load().oracle_rotate_adjoint_slice(n, float(theta), _ptr(a), _ptr(out))
     return out
+
+
+def rotate3_slice(img2d, theta: float) -> np.ndarray:
+    """Three-pass rotation of one (ny, nx) slice by theta: the exact quarter turn,
+    then 1D linear interpolation along x, y, x (zero padding), reading R13."""
+    a = _f64(img2d)
+    n = a.shape[0]
+    assert a.shape == (n, n)
+    out = np.empty_like(a)
+    _load().oracle_rotate3_slice(n, float(theta), _ptr(a), _ptr(out))
+    return out
+
+
+def rotate3_adjoint_slice(img2d, theta: float) -> np.ndarray:
+    """Transpose of :func:`rotate3_slice` (scatter form, passes in reverse order)."""
+    a = _f64(img2d)
+    n = a.shape[0]
+    out = np.empty_like(a)
+    _load().oracle_rotate3_adjoint_slice(n, float(theta), _ptr(a), _ptr(out))
+    return out
+
+
+ROTATIONS = {"bilinear": 0, "3pass": 1}
 
 
 def attenuation(mu_rot, dy: float) -> np.ndarray:
@@ -163,8 +188,9 @@ def _check(x_shape, mu, psf, angles):
     return nx, ny, nz, nview, px, pz, nview_psf
 
 
-def forward(x, mu, psf, dy: float, angles, nthreads: int = 0) -> np.ndarray:
-    """v = A x, Algorithm 1.  Returns (nview, nz, nx) float64."""
+def forward(x, mu, psf, dy: float, angles, nthreads: int = 0, rotation: str = "bilinear") -> np.ndarray:
+    """v = A x, Algorithm 1.  Returns (nview, nz, nx) float64.  rotation: "bilinear"
+    (R1, R2) or "3pass" (R13), the two image rotations of Section II-A."""
     x = _f64(x)
     mu = _f64(mu)
     psf = _f64(psf)
@@ -172,11 +198,11 @@ def forward(x, mu, psf, dy: float, angles, nthreads: int = 0) -> np.ndarray:
     nx, ny, nz, nview, px, pz, nvp = _check(x.shape, mu, psf, angles)
     v = np.empty((nview, nz, nx), dtype=np.float64)
     _load().oracle_forward(nx, ny, nz, nview, _ptr(x), _ptr(mu), float(dy), _ptr(psf), px, pz, nvp,
-                           _ptr(angles), _ptr(v), int(nthreads))
+                           _ptr(angles), _ptr(v), int(nthreads), ROTATIONS[rotation])
     return v
 
 
-def back(v, mu, psf, dy: float, angles, nthreads: int = 0) -> np.ndarray:
+def back(v, mu, psf, dy: float, angles, nthreads: int = 0, rotation: str = "bilinear") -> np.ndarray:
     """x = A' v, Algorithm 2 (literal transpose of :func:`forward`)."""
     v = _f64(v)
     mu = _f64(mu)
@@ -187,18 +213,19 @@ def back(v, mu, psf, dy: float, angles, nthreads: int = 0) -> np.ndarray:
     assert v.shape == (nview, nz, nx)
     x = np.empty((nz, ny, nx), dtype=np.float64)
     _load().oracle_back(nx, ny, nz, nview, _ptr(v), _ptr(mu), float(dy), _ptr(psf), px, pz, nvp,
-                        _ptr(angles), _ptr(x), int(nthreads))
+                        _ptr(angles), _ptr(x), int(nthreads), ROTATIONS[rotation])
     return x
 
 
-def sensitivity(mu, psf, dy: float, angles, nthreads: int = 0) -> np.ndarray:
+def sensitivity(mu, psf, dy: float, angles, nthreads: int = 0, rotation: str = "bilinear") -> np.ndarray:
     """s = A' 1 (the EM normaliser d(0) of Eq. (8))."""
     nz, ny, nx = np.shape(mu)
     ones = np.ones((len(angles), nz, nx), dtype=np.float64)
-    return back(ones, mu, psf, dy, angles, nthreads)
+    return back(ones, mu, psf, dy, angles, nthreads, rotation)
 
 
-def em_step(x, y, rbar, mu, psf, dy: float, angles, s=None, nthreads: int = 0) -> np.ndarray:
+def em_step(x, y, rbar, mu, psf, dy: float, angles, s=None, nthreads: int = 0,
+            rotation: str = "bilinear") -> np.ndarray:
     """One MLEM update, Eqs. (7)-(8) with beta = 0:
 
         x+ = x * A'(y / (A x + rbar)) / A'1.
@@ -209,14 +236,14 @@ def em_step(x, y, rbar, mu, psf, dy: float, angles, s=None, nthreads: int = 0) -
     x = _f64(x)
     y = _f64(y)
     if s is None:
-        s = sensitivity(mu, psf, dy, angles, nthreads)
-    ybar = forward(x, mu, psf, dy, angles, nthreads)
+        s = sensitivity(mu, psf, dy, angles, nthreads, rotation)
+    ybar = forward(x, mu, psf, dy, angles, nthreads, rotation)
     if rbar is not None:
         ybar = ybar + _f64(rbar)
     ratio = np.zeros_like(ybar)
     pos = ybar > 0
     ratio[pos] = y[pos] / ybar[pos]
-    e = back(ratio, mu, psf, dy, angles, nthreads)
+    e = back(ratio, mu, psf, dy, angles, nthreads, rotation)
     out = np.zeros_like(x)
     ok = s > 0
     out[ok] = x[ok] * e[ok] / s[ok]

@@ -38,6 +38,16 @@
  *      The adjoint is computed as the literal transpose; it does NOT rely
  *      on the PSF being symmetric.
  *   R5 the depth index j of p(:,:,j,l) is the depth in the rotated frame.
+ *   R13 the three-pass rotation (Section II-A names 3-pass 1D linear
+ *      interpolation as the alternative to bilinear rotation, without the
+ *      decomposition): theta = q*pi/2 + phi with q = nearest integer and
+ *      phi in [-pi/4, pi/4]; first the exact quarter turn q (the R1
+ *      convention at theta = q*pi/2), then three pull-backs, each a 1D
+ *      linear interpolation with zero padding:
+ *        along x at i + tan(phi/2)(j-c),
+ *        along y at j - sin(phi)(i-c),
+ *        along x at i + tan(phi/2)(j-c),
+ *      whose composition samples at R(-phi)(p-c)+c, the R1 convention.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -127,6 +137,122 @@ void oracle_rotate_adjoint_slice(int n, double theta, const double* in, double* 
 }
 
 /* ---------------------------------------------------------------------- */
+/* Three-pass rotation (reading R13).                                      */
+/* ---------------------------------------------------------------------- */
+
+/* theta = q*pi/2 + phi, q in 0..3, phi in [-pi/4, pi/4]. */
+static void quarter_split(double theta, int* q, double* phi)
+{
+    double r = nearbyint(theta / (M_PI / 2.0));
+    *phi = theta - r * (M_PI / 2.0);
+    *q = (int)(((long)r % 4 + 4) % 4);
+}
+
+/* Source pixel of output (i, j) under the quarter turn q (R1 at theta = q*pi/2). */
+static void quarter_source(int n, int q, int i, int j, int* si, int* sj)
+{
+    switch (q) {
+        case 0: *si = i; *sj = j; break;
+        case 1: *si = j; *sj = n - 1 - i; break;
+        case 2: *si = n - 1 - i; *sj = n - 1 - j; break;
+        default: *si = n - 1 - j; *sj = i; break;
+    }
+}
+
+/* Sample of the 1D signal f(0..n-1) (stride st) at position u by linear
+ * interpolation, zero outside. */
+static double interp1(const double* f, int n, size_t st, double u)
+{
+    int u0 = (int)floor(u);
+    double a = u - u0, acc = 0.0;
+    if (u0 >= 0 && u0 < n) acc += (1.0 - a) * f[st * (size_t)u0];
+    if (u0 + 1 >= 0 && u0 + 1 < n) acc += a * f[st * (size_t)(u0 + 1)];
+    return acc;
+}
+
+/* Transpose of interp1: f(u0) += (1-a) val, f(u0+1) += a val (in range). */
+static void interp1_adjoint(double* f, int n, size_t st, double u, double val)
+{
+    int u0 = (int)floor(u);
+    double a = u - u0;
+    if (u0 >= 0 && u0 < n) f[st * (size_t)u0] += (1.0 - a) * val;
+    if (u0 + 1 >= 0 && u0 + 1 < n) f[st * (size_t)(u0 + 1)] += a * val;
+}
+
+/* out = rotation of the n x n slice `in` by theta in three 1D passes. */
+void oracle_rotate3_slice(int n, double theta, const double* in, double* out)
+{
+    int q;
+    double phi;
+    quarter_split(theta, &q, &phi);
+    double c = 0.5 * (double)(n - 1), t = tan(0.5 * phi), s = sin(phi);
+    size_t nn = (size_t)n * n;
+    double* h = malloc(sizeof(double) * nn);
+    double* g = malloc(sizeof(double) * nn);
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            int si, sj;
+            quarter_source(n, q, i, j, &si, &sj);
+            h[(size_t)i + (size_t)n * j] = in[(size_t)si + (size_t)n * sj];
+        }
+    for (int j = 0; j < n; ++j) /* pass 1: along x */
+        for (int i = 0; i < n; ++i) g[(size_t)i + (size_t)n * j] = interp1(h + (size_t)n * j, n, 1, i + t * (j - c));
+    for (int j = 0; j < n; ++j) /* pass 2: along y */
+        for (int i = 0; i < n; ++i) h[(size_t)i + (size_t)n * j] = interp1(g + i, n, (size_t)n, j - s * (i - c));
+    for (int j = 0; j < n; ++j) /* pass 3: along x */
+        for (int i = 0; i < n; ++i) out[(size_t)i + (size_t)n * j] = interp1(h + (size_t)n * j, n, 1, i + t * (j - c));
+    free(h);
+    free(g);
+}
+
+/* Transpose of oracle_rotate3_slice: the passes' scatter transposes in
+ * reverse order, then the inverse quarter turn (out is overwritten). */
+void oracle_rotate3_adjoint_slice(int n, double theta, const double* in, double* out)
+{
+    int q;
+    double phi;
+    quarter_split(theta, &q, &phi);
+    double c = 0.5 * (double)(n - 1), t = tan(0.5 * phi), s = sin(phi);
+    size_t nn = (size_t)n * n;
+    double* h = calloc(nn, sizeof(double));
+    double* g = calloc(nn, sizeof(double));
+    for (int j = 0; j < n; ++j) /* pass 3 transposed */
+        for (int i = 0; i < n; ++i)
+            interp1_adjoint(h + (size_t)n * j, n, 1, i + t * (j - c), in[(size_t)i + (size_t)n * j]);
+    for (int j = 0; j < n; ++j) /* pass 2 transposed */
+        for (int i = 0; i < n; ++i) interp1_adjoint(g + i, n, (size_t)n, j - s * (i - c), h[(size_t)i + (size_t)n * j]);
+    memset(h, 0, sizeof(double) * nn);
+    for (int j = 0; j < n; ++j) /* pass 1 transposed */
+        for (int i = 0; i < n; ++i)
+            interp1_adjoint(h + (size_t)n * j, n, 1, i + t * (j - c), g[(size_t)i + (size_t)n * j]);
+    for (int j = 0; j < n; ++j) /* quarter turn transposed: a permutation */
+        for (int i = 0; i < n; ++i) {
+            int si, sj;
+            quarter_source(n, q, i, j, &si, &sj);
+            out[(size_t)si + (size_t)n * sj] = h[(size_t)i + (size_t)n * j];
+        }
+    free(h);
+    free(g);
+}
+
+/* The slice rotation of a projector: 0 bilinear (R1, R2), 1 three-pass (R13). */
+static void rotate_any(int mode, int n, double theta, const double* in, double* out)
+{
+    if (mode == 1)
+        oracle_rotate3_slice(n, theta, in, out);
+    else
+        oracle_rotate_slice(n, theta, in, out);
+}
+
+static void rotate_any_adjoint(int mode, int n, double theta, const double* in, double* out)
+{
+    if (mode == 1)
+        oracle_rotate3_adjoint_slice(n, theta, in, out);
+    else
+        oracle_rotate_adjoint_slice(n, theta, in, out);
+}
+
+/* ---------------------------------------------------------------------- */
 /* Accumulated attenuation, Eq. (1) (reading R3), in the rotated frame.   */
 /* mu_rot and mubar are nx*ny*nz arrays with the rotated-frame layout.     */
 /* ---------------------------------------------------------------------- */
@@ -184,14 +310,14 @@ void oracle_conv_adjoint_plane(int nx, int nz, const double* v, const double* p,
 /* One view of Algorithm 1 (forward projector).                            */
 /* ---------------------------------------------------------------------- */
 static void forward_one_view(int nx, int ny, int nz, const double* x, const double* mu, double dy,
-                             const double* psf_l, int px, int pz, double theta, double* v_l,
+                             const double* psf_l, int px, int pz, double theta, int rot_mode, double* v_l,
                              double* xr, double* mr, double* mbar, double* wplane, double* cplane)
 {
     size_t slice = (size_t)nx * ny;
     /* rotate x and mu slice by slice (each z-slice turns about the axial axis) */
     for (int k = 0; k < nz; ++k) {
-        oracle_rotate_slice(nx, theta, x + slice * k, xr + slice * k);
-        oracle_rotate_slice(nx, theta, mu + slice * k, mr + slice * k);
+        rotate_any(rot_mode, nx, theta, x + slice * k, xr + slice * k);
+        rotate_any(rot_mode, nx, theta, mu + slice * k, mr + slice * k);
     }
     oracle_attenuation(nx, ny, nz, dy, mr, mbar);
     memset(v_l, 0, sizeof(double) * (size_t)nx * nz);
@@ -206,10 +332,11 @@ static void forward_one_view(int nx, int ny, int nz, const double* x, const doub
 }
 
 /* v = A x over all views.  psf has nview_psf views (1 = view-invariant).
+ * rot_mode: 0 bilinear rotation, 1 three-pass rotation.
  * nthreads <= 0 uses the OpenMP default. */
 void oracle_forward(int nx, int ny, int nz, int nview, const double* x, const double* mu, double dy,
                     const double* psf, int px, int pz, int nview_psf, const double* angles, double* v,
-                    int nthreads)
+                    int nthreads, int rot_mode)
 {
     size_t vol = (size_t)nx * ny * nz, plane = (size_t)nx * nz, psfv = (size_t)px * pz * ny;
 #ifdef _OPENMP
@@ -227,7 +354,8 @@ void oracle_forward(int nx, int ny, int nz, int nview, const double* x, const do
 #endif
         for (int l = 0; l < nview; ++l) {
             const double* pl = psf + psfv * (nview_psf == 1 ? 0 : l);
-            forward_one_view(nx, ny, nz, x, mu, dy, pl, px, pz, angles[l], v + plane * l, xr, mr, mb, wp, cp);
+            forward_one_view(nx, ny, nz, x, mu, dy, pl, px, pz, angles[l], rot_mode, v + plane * l, xr, mr, mb, wp,
+                             cp);
         }
         free(xr); free(mr); free(mb); free(wp); free(cp);
     }
@@ -239,11 +367,11 @@ void oracle_forward(int nx, int ny, int nz, int nview, const double* x, const do
 /* xpart (nx*ny*nz) receives this view's contribution (overwritten).        */
 /* ---------------------------------------------------------------------- */
 static void back_one_view(int nx, int ny, int nz, const double* v_l, const double* mu, double dy,
-                          const double* psf_l, int px, int pz, double theta, double* xpart,
+                          const double* psf_l, int px, int pz, double theta, int rot_mode, double* xpart,
                           double* mr, double* mbar, double* t, double* wbar)
 {
     size_t slice = (size_t)nx * ny;
-    for (int k = 0; k < nz; ++k) oracle_rotate_slice(nx, theta, mu + slice * k, mr + slice * k);
+    for (int k = 0; k < nz; ++k) rotate_any(rot_mode, nx, theta, mu + slice * k, mr + slice * k);
     oracle_attenuation(nx, ny, nz, dy, mr, mbar);
     for (int j = 0; j < ny; ++j) {
         /* adjoint of (depth sum + blur at depth j): the same v plane for every j */
@@ -254,7 +382,7 @@ static void back_one_view(int nx, int ny, int nz, const double* v_l, const doubl
                 t[IDX3(i, j, k, nx, ny)] = wbar[i + (size_t)nx * k] * mbar[IDX3(i, j, k, nx, ny)];
     }
     /* adjoint of the rotation, slice by slice */
-    for (int k = 0; k < nz; ++k) oracle_rotate_adjoint_slice(nx, theta, t + slice * k, xpart + slice * k);
+    for (int k = 0; k < nz; ++k) rotate_any_adjoint(rot_mode, nx, theta, t + slice * k, xpart + slice * k);
 }
 
 /* x = A' v over all views (x is overwritten).  Views run in blocks of
@@ -262,7 +390,7 @@ static void back_one_view(int nx, int ny, int nz, const double* v_l, const doubl
  * result is the same for any thread count. */
 void oracle_back(int nx, int ny, int nz, int nview, const double* v, const double* mu, double dy,
                  const double* psf, int px, int pz, int nview_psf, const double* angles, double* x,
-                 int nthreads)
+                 int nthreads, int rot_mode)
 {
     size_t vol = (size_t)nx * ny * nz, plane = (size_t)nx * nz, psfv = (size_t)px * pz * ny;
 #ifdef _OPENMP
@@ -290,7 +418,8 @@ void oracle_back(int nx, int ny, int nz, int nview, const double* v, const doubl
             for (int b = 0; b < nb; ++b) {
                 int l = l0 + b;
                 const double* pl = psf + psfv * (nview_psf == 1 ? 0 : l);
-                back_one_view(nx, ny, nz, v + plane * l, mu, dy, pl, px, pz, angles[l], parts + vol * b, mr, mb, t, wb);
+                back_one_view(nx, ny, nz, v + plane * l, mu, dy, pl, px, pz, angles[l], rot_mode, parts + vol * b, mr,
+                              mb, t, wb);
             }
             free(mr); free(mb); free(t); free(wb);
         }

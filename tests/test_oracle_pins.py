@@ -15,6 +15,9 @@ a wrong padding rule in the oracle fails at least one of them:
   back A'       -> dense-matrix transpose of A (the paper's Section III-A
                    adjoint experiment, 336 x 384) and Eq. (2)
   EM            -> count preservation, fixed point, monotone likelihood
+  3-pass rotation -> shear algebra, scipy order-1 resampling per pass, lattice
+                   permutations, a blob turned by +theta, exact mass
+                   conservation, dense transpose (reading R13)
 """
 import os
 
@@ -425,3 +428,129 @@ def test_osem_iteration_advances_further_than_mlem():
     x_em = oracle.em_step(x0, y, None, prob.mu, psf, prob.dy, ang)
     x_os = oracle.osem_step(x0, y, None, prob.mu, psf, prob.dy, ang, 4)
     assert ll(x_os) > ll(x_em) > ll(x0)
+
+
+# ------------------------------------------------------------------ three-pass rotation (reading R13)
+# Section II-A names 3-pass 1D linear interpolation as the alternative image
+# rotation.  Pins: the shear product is the rotation matrix (algebra), each
+# pass is scipy's order-1 resampling along one axis, quarter turns are the
+# lattice permutations, a smooth blob turns by +theta about the centre, mass
+# is conserved exactly (each pass shifts rows), the adjoint is the dense
+# transpose, and the projector built on it is adjoint and count-preserving.
+def _shears(phi):
+    """(x, y) = (i - c, j - c) shear matrices Sx(tan(phi/2)), Sy(-sin(phi))."""
+    return (np.array([[1.0, np.tan(phi / 2)], [0.0, 1.0]]),
+            np.array([[1.0, 0.0], [-np.sin(phi), 1.0]]))
+
+
+def _scipy_pull(img, m):
+    """out(p) = img(m (p - c) + c) by scipy's order-1 resampling, zero outside; m acts on (x, y)."""
+    n = img.shape[0]
+    c = 0.5 * (n - 1)
+    mm = np.array([[m[1, 1], m[1, 0]], [m[0, 1], m[0, 0]]])  # ndimage order: (row j, column i)
+    off = np.array([c, c]) - mm @ np.array([c, c])
+    return ndimage.affine_transform(img, mm, offset=off, order=1, mode="grid-constant", cval=0.0)
+
+
+def test_rotation3_shear_product_is_the_rotation():
+    for phi in np.linspace(-np.pi / 4, np.pi / 4, 9):
+        sx, sy = _shears(phi)
+        r = np.array([[np.cos(phi), np.sin(phi)], [-np.sin(phi), np.cos(phi)]])  # R(-phi): output -> source
+        np.testing.assert_allclose(sx @ sy @ sx, r, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("theta", [0.3, 1.0, 2.2, 3.9, 5.5, -0.6])
+def test_rotation3_passes_match_scipy(theta):
+    rng = np.random.default_rng(21)
+    img = rng.uniform(-1, 1, (13, 13))
+    q = int(np.rint(theta / (np.pi / 2)))
+    phi = theta - q * np.pi / 2
+    sx, sy = _shears(phi)
+    ref = _scipy_pull(_scipy_pull(_scipy_pull(np.rot90(img, -(q % 4)), sx), sy), sx)
+    np.testing.assert_allclose(oracle.rotate3_slice(img, theta), ref, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("quarter", [0, 1, 2, 3, 4])
+def test_rotation3_quarter_turns_are_lattice_permutations(quarter):
+    rng = np.random.default_rng(22)
+    img = rng.uniform(0, 1, (10, 10))
+    got = oracle.rotate3_slice(img, quarter * np.pi / 2)
+    np.testing.assert_array_equal(got, np.rot90(img, -quarter))
+    np.testing.assert_array_equal(got, oracle.rotate_slice(img, quarter * np.pi / 2))
+
+
+@pytest.mark.parametrize("theta", [0.4, 1.9, 3.3, 5.0])
+def test_rotation3_turns_a_blob_by_theta(theta):
+    n, sig = 48, 3.0
+    c = 0.5 * (n - 1)
+    jj, ii = np.mgrid[0:n, 0:n].astype(np.float64)
+
+    def blob(px, py):
+        return np.exp(-((ii - px) ** 2 + (jj - py) ** 2) / (2 * sig * sig))
+
+    p0 = np.array([9.0, -5.0])
+    got = oracle.rotate3_slice(blob(*(p0 + c)), theta)
+    # content turns by +theta (reading R1): the centre moves to R(theta) p0
+    r = np.array([[np.cos(theta), -np.sin(theta)], [np.sin(theta), np.cos(theta)]])
+    want = blob(*(r @ p0 + c))
+    # three linear passes smooth a sigma = 3 px blob by a few percent of its peak;
+    # turning the other way (or about another centre) misses it by ~1
+    assert np.abs(got - want).max() < 0.05
+    assert np.abs(got - blob(*(r.T @ p0 + c))).max() > 0.5
+    # and it agrees with the bilinear rotation to the same accuracy
+    assert np.abs(got - oracle.rotate_slice(blob(*(p0 + c)), theta)).max() < 0.05
+
+
+@pytest.mark.parametrize("theta", [0.35, 2.6, 4.1])
+def test_rotation3_conserves_mass_inside_the_circle(theta):
+    n = 32
+    c = 0.5 * (n - 1)
+    jj, ii = np.mgrid[0:n, 0:n]
+    rng = np.random.default_rng(23)
+    img = rng.uniform(0, 1, (n, n)) * (((ii - c) ** 2 + (jj - c) ** 2) < (0.3 * n) ** 2)
+    got = oracle.rotate3_slice(img, theta)
+    assert abs(got.sum() - img.sum()) <= 1e-12 * img.sum()
+    # bilinear rotation is only approximately mass-preserving
+    assert abs(oracle.rotate_slice(img, theta).sum() - img.sum()) > 1e-6 * img.sum()
+
+
+@pytest.mark.parametrize("theta", [0.4, 2.0, 4.4])
+def test_rotation3_adjoint_is_dense_transpose(theta):
+    n = 8
+    R = np.stack([oracle.rotate3_slice(e.reshape(n, n), theta).ravel() for e in np.eye(n * n)], axis=1)
+    Rt = np.stack([oracle.rotate3_adjoint_slice(e.reshape(n, n), theta).ravel() for e in np.eye(n * n)], axis=1)
+    np.testing.assert_allclose(Rt, R.T, rtol=0, atol=1e-15)
+
+
+def test_forward3_quarter_turn_views_equal_bilinear():
+    prob = synthetic.random_problem(24, nx=12, nz=4, nview=4, px=3, pz=5, mu_scale=0.2)
+    ang = np.arange(4) * np.pi / 2
+    a = oracle.forward(prob.x, prob.mu, prob.psf, 1.0, ang, rotation="3pass")
+    b = oracle.forward(prob.x, prob.mu, prob.psf, 1.0, ang, rotation="bilinear")
+    np.testing.assert_array_equal(a, b)
+
+
+def test_dense_adjoint3_small():
+    prob = synthetic.random_problem(25, nx=8, nz=4, nview=5, px=3, pz=3, symmetric=False, mu_scale=0.3)
+    ang = oracle.default_angles(5) + 0.2
+    N, M = 8 * 8 * 4, 8 * 4 * 5
+    A = np.stack([oracle.forward(e.reshape(4, 8, 8), prob.mu, prob.psf, 1.0, ang, nthreads=1, rotation="3pass").ravel()
+                  for e in np.eye(N)], axis=1)
+    B = np.stack([oracle.back(e.reshape(5, 4, 8), prob.mu, prob.psf, 1.0, ang, nthreads=1, rotation="3pass").ravel()
+                  for e in np.eye(M)], axis=1)
+    assert np.linalg.norm(A.T - B) / np.linalg.norm(A) < 1e-14
+    # a different operator from the bilinear projector away from quarter turns
+    Ab = np.stack([oracle.forward(e.reshape(4, 8, 8), prob.mu, prob.psf, 1.0, ang, nthreads=1).ravel()
+                   for e in np.eye(N)], axis=1)
+    assert np.linalg.norm(A - Ab) > 1e-3 * np.linalg.norm(A)
+
+
+def test_em3_preserves_counts_with_zero_background():
+    prob, psf, ang = _em_problem()
+    rng = np.random.default_rng(26)
+    y = rng.poisson(5.0, (prob.nview, 6, 16)).astype(np.float64)
+    s = oracle.sensitivity(prob.mu, psf, prob.dy, ang, rotation="3pass")
+    x = np.ones((6, 16, 16))
+    for _ in range(2):
+        x = oracle.em_step(x, y, None, prob.mu, psf, prob.dy, ang, s=s, rotation="3pass")
+        assert abs(np.sum(s * x) - y.sum()) <= 1e-11 * y.sum()
