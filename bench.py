@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--path", choices=["separable", "direct"], default="separable")
     ap.add_argument("--direct-steps", type=int, default=3, help="steps of the full-PSF path reported beside (0: skip)")
+    ap.add_argument("--rot3-steps", type=int, default=20,
+                    help="steps with the three-pass rotation reported beside (0: skip)")
     ap.add_argument("--cpu-views", type=int, default=0, help="views in the CPU baseline sample (0: auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default launch shapes")
@@ -118,7 +120,7 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- workload
-def make_workload(device, path, nview=NVIEW, autotune=True):
+def make_workload(device, path, nview=NVIEW, autotune=True, rotation="bilinear"):
     import torch
 
     from paper_2301_09710_gb300 import SpectPlan, synthetic
@@ -126,7 +128,8 @@ def make_workload(device, path, nview=NVIEW, autotune=True):
     prob = synthetic.config2(seed=0, nx=NX, nz=NZ, nview=nview, psf_size=PSF)
     sep = path == "separable"
     if sep:
-        plan = SpectPlan(NX, NZ, nview, mu=prob.mu, dy=prob.dy, fx=prob.fx, fz=prob.fz, device=device)
+        plan = SpectPlan(NX, NZ, nview, mu=prob.mu, dy=prob.dy, fx=prob.fx, fz=prob.fz, device=device,
+                         rotation=rotation)
         if autotune:
             plan.autotune()  # the library's launch-shape autotuner (timed on this device, outside the timed region)
     else:
@@ -339,27 +342,40 @@ def run_ours(args):
            "copies": "pinned host buffers; uploads of step k+1 and download of step k overlap the EM steps",
            "serial_value": world * args.steps / (s_ms / 1e3)}
 
-    direct = None
-    if args.direct_steps > 0 and args.path == "separable":
-        plan.close()
-        _, dplan, _, _, _ = make_workload(device, "direct")
-        xd2 = torch.from_numpy(x0_h).to(device)
-        dplan.em_step(xd2, y, rbar, niter=1)
+    def side_ms(splan, steps):
+        """Average device time of one EM iteration of another plan of the workload (L2 flushed between)."""
+        xs = torch.from_numpy(x0_h).to(device)
+        splan.em_step(xs, y, rbar, niter=1)
         torch.cuda.synchronize()
         dl = []
-        for _ in range(args.direct_steps):
+        for _ in range(steps):
             flush.fill_(1.0)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            dplan.em_step(xd2, y, rbar, niter=1)
+            splan.em_step(xs, y, rbar, niter=1)
             b.record(stream)
             b.synchronize()
             dl.append(a.elapsed_time(b))
-        dms = sum(dl) / len(dl)
+        splan.check()
+        return sum(dl) / len(dl)
+
+    direct = rot3 = None
+    if args.path == "separable" and (args.direct_steps > 0 or args.rot3_steps > 0):
+        plan.close()
+    if args.direct_steps > 0 and args.path == "separable":
+        _, dplan, _, _, _ = make_workload(device, "direct")
+        dms = side_ms(dplan, args.direct_steps)
         direct = {"value": 1e3 / dms, "unit": UNIT, "ms_per_step": dms,
                   "gflop_per_pair": 2 * algorithmic_flops("conv_fwd", NVIEW, False) / 1e9,
                   "note": "same workload with the full 37x37 PSF stack (direct 2D blur, no separability)"}
         dplan.close()
+    if args.rot3_steps > 0 and args.path == "separable" and args.nview == NVIEW:
+        _, rplan, _, _, _ = make_workload(device, "separable", rotation="3pass")
+        rms = side_ms(rplan, args.rot3_steps)
+        rot3 = {"value": 1e3 / rms, "unit": UNIT, "ms_per_step": rms, "launch_shape": rplan.tuning,
+                "note": "same workload with the three-pass rotation (quarter turn, then 1D linear "
+                        "interpolation along x, y, x) instead of bilinear rotation"}
+        rplan.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -380,6 +396,8 @@ def run_ours(args):
                "cpu_baseline": cpu, "wall_s_timed_region": wall}
         if direct:
             out["direct_path"] = direct
+        if rot3:
+            out["rot3_path"] = rot3
         print(json.dumps(out))
     if dist:
         dist.barrier()

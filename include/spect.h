@@ -82,7 +82,20 @@ enum {
      * per view and stream views through a small work slab, instead of
      * caching the attenuation factors of every view (nview * nx*ny*nz floats)
      * and using the fused kernels. */
-    SPECT_PLAN_LOW_MEMORY = 1u << 1
+    SPECT_PLAN_LOW_MEMORY = 1u << 1,
+    /* Rotate the image and the attenuation map by three 1D linear
+     * interpolation passes instead of bilinear interpolation (Section II-A
+     * implements both): theta = q*pi/2 + phi, q the nearest integer and
+     * phi in [-pi/4, pi/4]; the exact quarter turn q, then pull-backs along
+     * x at i + tan(phi/2)(j-c), along y at j - sin(phi)(i-c) and along x at
+     * i + tan(phi/2)(j-c), each with zero padding, c = (nx-1)/2.  A' is the
+     * exact transpose (the passes' transposes in reverse order).  Fused
+     * plans only: with SPECT_PLAN_LOW_MEMORY, or when the fused kernels do
+     * not fit the geometry, spect_plan_create returns SPECT_EUNSUPPORTED.
+     * The plan holds four more rotation tables (4 * nview*ny*(5nx) floats)
+     * and two per-view pass buffers (2 * chunk views * ny*(nx*nz rounded
+     * up to 4) floats). */
+    SPECT_PLAN_ROTATION_3PASS = 1u << 2
 };
 
 /*

@@ -21,6 +21,8 @@ STATUS = {0: "SPECT_OK", 1: "SPECT_EINVAL", 2: "SPECT_ENOMEM", 3: "SPECT_ECUDA",
           5: "SPECT_EUNSUPPORTED"}
 SPECT_PLAN_PREFER_SEPARABLE = 1
 SPECT_PLAN_LOW_MEMORY = 2
+SPECT_PLAN_ROTATION_3PASS = 4
+ROTATIONS = ("bilinear", "3pass")
 KERNEL_CLASSES = ["rotate_atten", "conv_fwd", "conv_adj", "rotate_adj", "other"]
 
 

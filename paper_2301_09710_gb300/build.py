@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libspect.so")
-SOURCES = ["plan.cu", "rotate.cu", "conv.cu", "fused.cu", "gather.cu", "rotpatch.cu", "peak.cu", "static_fwd.cu"]
+SOURCES = ["plan.cu", "rotate.cu", "conv.cu", "fused.cu", "gather.cu", "rotpatch.cu", "rot3.cu", "peak.cu",
+           "static_fwd.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills",
               "--expt-relaxed-constexpr"]

@@ -381,7 +381,7 @@ constexpr int kRotThreads = 512;
 // instead of as per-element global loads, when the two planes fit.
 template <int P, bool MUS>
 __global__ void __launch_bounds__(kRotThreads, 2) k_rot_fwd(Geometry g, FusedDims d, const float* __restrict__ rtab,
-                                                         const float* __restrict__ xt,
+                                                         const float* __restrict__ xt, size_t xt_vs,
                                                          const float* __restrict__ mubar, float* __restrict__ wsl,
                                                          int l0, int* err)
 {
@@ -397,6 +397,7 @@ __global__ void __launch_bounds__(kRotThreads, 2) k_rot_fwd(Geometry g, FusedDim
     const int j = blockIdx.x, v = blockIdx.y, l = l0 + v;
     const int pln = nx * nz;
     const int wp = d.wpf;
+    xt += (size_t)v * xt_vs;  // per-view input volumes (the three-pass rotation), else one
     const int wcols = d.nib * Sep<P>::CX + 2 * C;
     const float* tab = rtab + ((size_t)l * ny + j) * d.ts;
     const float* mb = mubar + ((size_t)l * ny + j) * d.ps;
@@ -1341,7 +1342,9 @@ cudaError_t rot_launch(const spect_plan_s& Pl, const float* xt, int l0, int nv, 
     auto kern = mus ? k_rot_fwd<P, true> : k_rot_fwd<P, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(Pl.g.ny, nv), kRotThreads, smem, st>>>(Pl.g, d, Pl.rtab, xt, Pl.mubar, Pl.slab, l0, Pl.err);
+    // the three-pass rotation hands each view its own pass-2 volume
+    const size_t xvs = Pl.rot3 ? (size_t)Pl.g.nx * Pl.g.ny * Pl.g.nz : 0;
+    kern<<<dim3(Pl.g.ny, nv), kRotThreads, smem, st>>>(Pl.g, d, Pl.rtab, xt, xvs, Pl.mubar, Pl.slab, l0, Pl.err);
     return cudaGetLastError();
 }
 
@@ -1567,13 +1570,15 @@ cudaError_t launch_adj_rot_t(const spect_plan_s& P, int l0, int nv, float* out, 
     const bool vec4 = (P.g.nz % 4) == 0;
     const size_t n = (size_t)P.g.nx * P.g.ny * (vec4 ? P.g.nz / 4 : P.g.nz);
     const unsigned blocks = (unsigned)((n + 255) / 256);
+    // the three-pass rotation's lists read its pass-1 transposed input
+    const float* src = P.rot3 ? P.r3_b : P.slab;
     switch (P.adj_max) {
 #define SPECT_ADJ(M)                                                                                                 \
     case M:                                                                                                          \
         if (vec4)                                                                                                    \
-            k_adj_rot_t<M, 4><<<blocks, 256, 0, st>>>(P.g, P.ps, P.adjf, P.slab, l0, nv, out, accumulate, em); \
+            k_adj_rot_t<M, 4><<<blocks, 256, 0, st>>>(P.g, P.ps, P.adjf, src, l0, nv, out, accumulate, em);    \
         else                                                                                                         \
-            k_adj_rot_t<M, 1><<<blocks, 256, 0, st>>>(P.g, P.ps, P.adjf, P.slab, l0, nv, out, accumulate, em); \
+            k_adj_rot_t<M, 1><<<blocks, 256, 0, st>>>(P.g, P.ps, P.adjf, src, l0, nv, out, accumulate, em);    \
         break;
         SPECT_ADJ(1) SPECT_ADJ(2) SPECT_ADJ(3) SPECT_ADJ(4) SPECT_ADJ(5) SPECT_ADJ(6) SPECT_ADJ(7) SPECT_ADJ(8)
 #undef SPECT_ADJ

@@ -134,7 +134,7 @@ void free_plan(spect_plan_s* P, cudaStream_t st)
     for (cudaEvent_t e : P->evpool) cudaEventDestroy(e);
     void* ptrs[] = {P->mu, P->psf, P->psf_adj, P->fx, P->fz, P->fx_adj, P->fz_adj, P->rot, P->adj_off, P->adj,
                     P->slab, P->e, P->ratio, P->s, P->mubar, P->xt, P->et, P->st, P->part, P->adjf, P->err, P->rtab, P->ut,
-                    P->gboxes, P->gent, P->rboxes};
+                    P->gboxes, P->gent, P->rboxes, P->r3_p1, P->r3_p2, P->r3_t3, P->r3_t2, P->r3_a, P->r3_b};
     for (void* p : ptrs) raw_free(P, p, st);
     delete P;
 }
@@ -253,8 +253,13 @@ spect_status fast_forward(spect_plan_s* P, const float* xt, float* v, const floa
     const int nview = P->g.nview;
     for (int l0 = 0; l0 < nview; l0 += P->chunk) {
         const int nv = std::min(P->chunk, nview - l0);
+        if (P->rot3) {  // passes 1 and 2 of the three-pass rotation; pass 3 is the rotation kernel
+            SPECT_CUDA_TRY(counted(P, SPECT_K_ROTATE_ATTEN, st,
+                                   [&] { return spect::launch_rot3_forward_passes(*P, xt, l0, nv, st); }),
+                           "three-pass rotation launch");
+        }
         SPECT_CUDA_TRY(counted(P, SPECT_K_ROTATE_ATTEN, st,
-                               [&] { return spect::launch_fused_rotate(*P, xt, l0, nv, st); }),
+                               [&] { return spect::launch_fused_rotate(*P, P->rot3 ? P->r3_b : xt, l0, nv, st); }),
                        "rotation launch");
         SPECT_CUDA_TRY(counted(P, SPECT_K_CONV_FWD, st,
                                [&] { return spect::launch_fused_forward(*P, xt, l0, nv, st); }),
@@ -274,6 +279,10 @@ spect_status fast_back(spect_plan_s* P, const float* v, float* out_t, spect::EmA
         const bool last = l0 + nv >= nview;
         SPECT_CUDA_TRY(counted(P, SPECT_K_CONV_ADJ, st, [&] { return spect::launch_fused_adjoint(*P, v, l0, nv, st); }),
                        "fused adjoint launch");
+        if (P->rot3)  // transposed passes 3 and 2; the list gather does the transposed pass 1
+            SPECT_CUDA_TRY(counted(P, SPECT_K_ROTATE_ADJ, st,
+                                   [&] { return spect::launch_rot3_adjoint_passes(*P, l0, nv, st); }),
+                           "three-pass adjoint rotation launch");
         spect::EmArgs e = em;
         if (!last) e.x = nullptr;
         SPECT_CUDA_TRY(counted(P, SPECT_K_ROTATE_ADJ, st,
@@ -359,6 +368,8 @@ size_t plan_bytes_bound(const spect_plan_s& P)
         // patch gather: boxes and box-local entries (at most 8 per list)
         const size_t np = (size_t)((g.nx + 7) / 8) * ((g.ny + 7) / 8) * g.nview;
         b += np * 16 + np * 64 * 8 * sizeof(spect::AdjEntry) + np * 16;  // + rotation boxes
+        if (P.rot3)  // four more tables and two per-view pass buffers
+            b += 4 * (size_t)g.nview * g.ny * P.ts * F + 2 * (size_t)g.ny * P.ps * chunk * F;
     }
     return b;
 }
@@ -390,6 +401,7 @@ spect_status spect_plan_bytes(int nx, int ny, int nz, int nview, int px, int pz,
     P.ts = (5 * nx + 3) & ~3;
     P.cls_x = 3;
     P.cls_z = nz >= 2 ? 3 : 1;
+    P.rot3 = (flags & SPECT_PLAN_ROTATION_3PASS) != 0;
     if (P.separable && !(flags & SPECT_PLAN_LOW_MEMORY)) {
         P.bucket = spect::fused_bucket(g, (size_t)smem_optin, &P.fused_nT);
         P.fast = P.bucket > 0;
@@ -418,7 +430,7 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
     if (!(dy >= 0.f) || !isfinite(dy)) return fail(SPECT_EINVAL, "dy must be finite and >= 0");
     if ((psf_fx == nullptr) != (psf_fz == nullptr)) return fail(SPECT_EINVAL, "give both psf_fx and psf_fz or neither");
     if (!psf && !psf_fx) return fail(SPECT_EINVAL, "no PSF given (psf or psf_fx/psf_fz)");
-    if ((flags & ~(unsigned)(SPECT_PLAN_PREFER_SEPARABLE | SPECT_PLAN_LOW_MEMORY)) != 0)
+    if ((flags & ~(unsigned)(SPECT_PLAN_PREFER_SEPARABLE | SPECT_PLAN_LOW_MEMORY | SPECT_PLAN_ROTATION_3PASS)) != 0)
         return fail(SPECT_EINVAL, "unknown flag bits");
     const void* ins[] = {mu, psf, psf_fx, psf_fz};
     for (const void* p : ins)
@@ -481,6 +493,11 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
         P->bucket = spect::fused_dir_bucket(g, (size_t)smem_optin);
         P->fast = P->bucket > 0;
         P->fused_nT = 1;
+    }
+    P->rot3 = (flags & SPECT_PLAN_ROTATION_3PASS) != 0;
+    if (P->rot3 && !P->fast) {
+        free_plan(P);
+        return fail(SPECT_EUNSUPPORTED, "the three-pass rotation runs on the fused kernels (not a low-memory plan)");
     }
     if (P->separable) {
         P->sep_tk = spect::choose_sep_tile(g, P->cls_z, (size_t)smem_optin);
@@ -558,8 +575,9 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
         PLAN_TRY(e2, "adjacency counts download");
         PLAN_TRY(e3, "adjacency max download");
         PLAN_TRY(e4, "adjacency count");
+        if (P->rot3) mx = std::max(mx, 2);  // two entries per (voxel, view) for the three-pass lists
         P->adj_max = mx;
-        if (P->fast && mx > 8) P->fast = 0;  // fixed-length lists are instantiated up to 8 entries
+        if (P->fast && mx > 8 && !P->rot3) P->fast = 0;  // fixed-length lists are instantiated up to 8 entries
         if (P->fast) {
             PLAN_ALLOC(P->adjf, nlist * (size_t)std::max(mx, 1), "adjacency lists");
             if (mx < 1) P->adj_max = 1;
@@ -618,11 +636,26 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
         P->part_cap = nproj * (size_t)spect::fused_groups(*P);
         // mu in the [j][i][k] layout (temporary, the slab serves as scratch)
         PLAN_TRY(spect::launch_transpose(P->mu, P->slab, nz, (int)nxy, st), "mu transpose launch");
-        PLAN_TRY(spect::launch_mubar_cache(*P, P->slab, st), "attenuation cache launch");
         PLAN_ALLOC(P->rtab, (size_t)nview * ny * P->ts, "rotation tables");
-        PLAN_TRY(spect::launch_rot_tables(*P, st), "rotation table launch");
-        PLAN_TRY(spect::build_gather(*P, st), "patch gather set-up");
-        PLAN_TRY(spect::build_rotpatch(*P, st), "patch rotation set-up");
+        if (P->rot3) {
+            // three passes: tables of passes 1, 2 and the transposed 3, 2 (rtab holds
+            // pass 3), per-view pass buffers, lists of the transposed pass 1 (in adjf),
+            // and the attenuation cache from mu turned the same way
+            const size_t tab = (size_t)nview * ny * P->ts;
+            PLAN_ALLOC(P->r3_p1, tab, "three-pass tables");
+            PLAN_ALLOC(P->r3_p2, tab, "three-pass tables");
+            PLAN_ALLOC(P->r3_t3, tab, "three-pass tables");
+            PLAN_ALLOC(P->r3_t2, tab, "three-pass tables");
+            P->r3_cap = (size_t)ny * P->ps * P->chunk;
+            PLAN_ALLOC(P->r3_a, P->r3_cap, "three-pass buffers");
+            PLAN_ALLOC(P->r3_b, P->r3_cap, "three-pass buffers");
+            PLAN_TRY(spect::build_rot3(*P, angles, P->slab, st), "three-pass rotation set-up");
+        } else {
+            PLAN_TRY(spect::launch_mubar_cache(*P, P->slab, st), "attenuation cache launch");
+            PLAN_TRY(spect::launch_rot_tables(*P, st), "rotation table launch");
+            PLAN_TRY(spect::build_gather(*P, st), "patch gather set-up");
+            PLAN_TRY(spect::build_rotpatch(*P, st), "patch rotation set-up");
+        }
     }
     PLAN_TRY(cudaStreamSynchronize(st), "plan set-up");
     *out = P;
@@ -927,6 +960,13 @@ spect_status reconfigure(spect_plan_s* P, int J, int adj_J, int tiles, cudaStrea
         P->adj_J = oaJ;
         P->fused_nT = ont;
         return r;
+    }
+    if (P->rot3) {  // the pass buffers hold the chunk's views
+        const size_t need = (size_t)g.ny * P->ps * chunk;
+        size_t cap_b = P->r3_cap;  // r3_cap grows only once both buffers have
+        r = realloc_floats(P, &P->r3_b, &cap_b, need, st, "three-pass buffers");
+        if (r == SPECT_OK) r = realloc_floats(P, &P->r3_a, &P->r3_cap, need, st, "three-pass buffers");
+        if (r != SPECT_OK) return r;
     }
     P->chunk = chunk;
     P->adj_chunk = P->adj_chunk_req > 0 ? std::min(P->adj_chunk_req, chunk) : chunk;

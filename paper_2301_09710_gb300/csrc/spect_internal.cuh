@@ -103,6 +103,17 @@ struct spect_plan_s {
     // used instead of k_rot_fwd when rotpatch_on != 0 (chosen by the autotuner)
     int rotpatch = 0;
     int rotpatch_on = 0;
+    // three-pass rotation (rot3.cu): tables of passes 1 and 2 and of the
+    // transposed passes 3 and 2 ([l][j] blocks like rtab, which then holds
+    // pass 3), and two per-view volume buffers of the passes (chunk views each)
+    int rot3 = 0;
+    float* r3_p1 = nullptr;
+    float* r3_p2 = nullptr;
+    float* r3_t3 = nullptr;
+    float* r3_t2 = nullptr;
+    float* r3_a = nullptr;
+    float* r3_b = nullptr;
+    size_t r3_cap = 0;           // floats of each of r3_a, r3_b
     int4* rboxes = nullptr;      // [patch][l] source box of x_t (i0, j0, width, height)
     int rbw = 0, rbh = 0;
     CUtensorMap rmap_x, rmap_mu; // x_t (k, i, j) and the attenuation cache (k, i, plane)
@@ -363,6 +374,10 @@ cudaError_t launch_build_adjacency_fixed(const spect_plan_s& P, cudaStream_t st)
 cudaError_t launch_rot_tables(const spect_plan_s& P, cudaStream_t st);
 cudaError_t launch_fused_forward(const spect_plan_s& P, const float* xt, int l0, int nv, cudaStream_t st);
 cudaError_t launch_fused_rotate(const spect_plan_s& P, const float* xt, int l0, int nv, cudaStream_t st);
+// three-pass rotation (rot3.cu)
+cudaError_t build_rot3(spect_plan_s& P, const double* angles, const float* mu_t, cudaStream_t st);
+cudaError_t launch_rot3_forward_passes(const spect_plan_s& P, const float* xt, int l0, int nv, cudaStream_t st);
+cudaError_t launch_rot3_adjoint_passes(const spect_plan_s& P, int l0, int nv, cudaStream_t st);
 size_t fused_slab_per_view(const spect_plan_s& P);
 cudaError_t launch_fused_adjoint(const spect_plan_s& P, const float* v, int l0, int nv, cudaStream_t st);
 cudaError_t launch_fwd_reduce(const spect_plan_s& P, float* v, const float* em_y, const float* em_rbar,

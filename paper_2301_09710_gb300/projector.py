@@ -68,22 +68,33 @@ def forward_static(x, nview: int, fx, fz, mu=None, dy: float = 1.0, angles=None,
     return out
 
 
+def _rotation_flag(rotation: str) -> int:
+    if rotation not in _lib.ROTATIONS:
+        raise ValueError(f"rotation must be one of {_lib.ROTATIONS}")
+    return _lib.SPECT_PLAN_ROTATION_3PASS if rotation == "3pass" else 0
+
+
 def plan_bytes(nx: int, nz: int, nview: int, px: int, pz: int, nview_psf: int = 1, separable: bool = True,
-               low_memory: bool = False) -> int:
+               low_memory: bool = False, rotation: str = "bilinear") -> int:
     """Upper bound of the device bytes a plan of this geometry allocates (no allocation)."""
     lib = _lib.load()
     out = ctypes.c_size_t()
-    flags = _lib.SPECT_PLAN_LOW_MEMORY if low_memory else 0
+    flags = (_lib.SPECT_PLAN_LOW_MEMORY if low_memory else 0) | _rotation_flag(rotation)
     _lib.check(lib.spect_plan_bytes(int(nx), int(nx), int(nz), int(nview), int(px), int(pz), int(nview_psf),
                                     int(bool(separable)), flags, ctypes.byref(out)))
     return out.value
 
 
 class SpectPlan:
-    """The operator A of one geometry (Algorithm 1 inputs) on one GPU."""
+    """The operator A of one geometry (Algorithm 1 inputs) on one GPU.
+
+    rotation: "bilinear" (default) or "3pass", the two image rotations of
+    Section II-A (the three-pass one on the fused kernels only).
+    """
 
     def __init__(self, nx: int, nz: int, nview: int, mu=None, dy: float = 1.0, psf=None, fx=None, fz=None,
-                 angles=None, prefer_separable: bool = True, low_memory: bool = False, device=None, stream=None):
+                 angles=None, prefer_separable: bool = True, low_memory: bool = False, device=None, stream=None,
+                 rotation: str = "bilinear"):
         self.lib = _lib.load()
         self.device = torch.device(device if device is not None else "cuda")
         self.nx = self.ny = int(nx)
@@ -104,7 +115,8 @@ class SpectPlan:
             ang = self._angles.ctypes.data_as(ctypes.c_void_p)
         handle = ctypes.c_void_p()
         flags = (_lib.SPECT_PLAN_PREFER_SEPARABLE if prefer_separable else 0) | \
-            (_lib.SPECT_PLAN_LOW_MEMORY if low_memory else 0)
+            (_lib.SPECT_PLAN_LOW_MEMORY if low_memory else 0) | _rotation_flag(rotation)
+        self.rotation = rotation
         with torch.cuda.device(self.device):
             _lib.check(self.lib.spect_plan_create(
                 ctypes.byref(handle), self.nx, self.ny, self.nz, self.nview, _ptr(self._mu), ctypes.c_float(dy),
