@@ -1570,8 +1570,8 @@ cudaError_t launch_adj_rot_t(const spect_plan_s& P, int l0, int nv, float* out, 
     const bool vec4 = (P.g.nz % 4) == 0;
     const size_t n = (size_t)P.g.nx * P.g.ny * (vec4 ? P.g.nz / 4 : P.g.nz);
     const unsigned blocks = (unsigned)((n + 255) / 256);
-    // the three-pass rotation's lists read its pass-1 transposed input
-    const float* src = P.rot3 ? P.r3_b : P.slab;
+    // the three-pass rotation's lists read the output of its transposed pass 3
+    const float* src = P.rot3 ? P.r3_a : P.slab;
     switch (P.adj_max) {
 #define SPECT_ADJ(M)                                                                                                 \
     case M:                                                                                                          \

@@ -134,7 +134,7 @@ void free_plan(spect_plan_s* P, cudaStream_t st)
     for (cudaEvent_t e : P->evpool) cudaEventDestroy(e);
     void* ptrs[] = {P->mu, P->psf, P->psf_adj, P->fx, P->fz, P->fx_adj, P->fz_adj, P->rot, P->adj_off, P->adj,
                     P->slab, P->e, P->ratio, P->s, P->mubar, P->xt, P->et, P->st, P->part, P->adjf, P->err, P->rtab, P->ut,
-                    P->gboxes, P->gent, P->rboxes, P->r3_p1, P->r3_p2, P->r3_t3, P->r3_t2, P->r3_a, P->r3_b};
+                    P->gboxes, P->gent, P->rboxes, P->r3_p12, P->r3_t3, P->r3_a, P->r3_b};
     for (void* p : ptrs) raw_free(P, p, st);
     delete P;
 }
@@ -368,8 +368,8 @@ size_t plan_bytes_bound(const spect_plan_s& P)
         // patch gather: boxes and box-local entries (at most 8 per list)
         const size_t np = (size_t)((g.nx + 7) / 8) * ((g.ny + 7) / 8) * g.nview;
         b += np * 16 + np * 64 * 8 * sizeof(spect::AdjEntry) + np * 16;  // + rotation boxes
-        if (P.rot3)  // four more tables and two per-view pass buffers
-            b += 4 * (size_t)g.nview * g.ny * P.ts * F + 2 * (size_t)g.ny * P.ps * chunk * F;
+        if (P.rot3)  // two more tables and two per-view pass buffers
+            b += (size_t)g.nview * g.ny * (8 * (size_t)g.nx + P.ts) * F + 2 * (size_t)g.ny * P.ps * chunk * F;
     }
     return b;
 }
@@ -575,7 +575,7 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
         PLAN_TRY(e2, "adjacency counts download");
         PLAN_TRY(e3, "adjacency max download");
         PLAN_TRY(e4, "adjacency count");
-        if (P->rot3) mx = std::max(mx, 2);  // two entries per (voxel, view) for the three-pass lists
+        if (P->rot3) mx = std::max(mx, 4);  // four entries per (voxel, view) for the three-pass lists
         P->adj_max = mx;
         if (P->fast && mx > 8 && !P->rot3) P->fast = 0;  // fixed-length lists are instantiated up to 8 entries
         if (P->fast) {
@@ -638,14 +638,12 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
         PLAN_TRY(spect::launch_transpose(P->mu, P->slab, nz, (int)nxy, st), "mu transpose launch");
         PLAN_ALLOC(P->rtab, (size_t)nview * ny * P->ts, "rotation tables");
         if (P->rot3) {
-            // three passes: tables of passes 1, 2 and the transposed 3, 2 (rtab holds
-            // pass 3), per-view pass buffers, lists of the transposed pass 1 (in adjf),
-            // and the attenuation cache from mu turned the same way
-            const size_t tab = (size_t)nview * ny * P->ts;
-            PLAN_ALLOC(P->r3_p1, tab, "three-pass tables");
-            PLAN_ALLOC(P->r3_p2, tab, "three-pass tables");
-            PLAN_ALLOC(P->r3_t3, tab, "three-pass tables");
-            PLAN_ALLOC(P->r3_t2, tab, "three-pass tables");
+            // three passes: the 4-tap table of passes 1 + 2, the table of the
+            // transposed pass 3 (rtab holds pass 3), per-view pass buffers, the lists
+            // of the transposed passes 2 and 1 (in adjf), and the attenuation cache
+            // from mu turned the same way
+            PLAN_ALLOC(P->r3_p12, (size_t)nview * ny * spect::rot3_ts4(nx), "three-pass tables");
+            PLAN_ALLOC(P->r3_t3, (size_t)nview * ny * P->ts, "three-pass tables");
             P->r3_cap = (size_t)ny * P->ps * P->chunk;
             PLAN_ALLOC(P->r3_a, P->r3_cap, "three-pass buffers");
             PLAN_ALLOC(P->r3_b, P->r3_cap, "three-pass buffers");

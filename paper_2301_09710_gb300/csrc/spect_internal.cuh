@@ -103,14 +103,12 @@ struct spect_plan_s {
     // used instead of k_rot_fwd when rotpatch_on != 0 (chosen by the autotuner)
     int rotpatch = 0;
     int rotpatch_on = 0;
-    // three-pass rotation (rot3.cu): tables of passes 1 and 2 and of the
-    // transposed passes 3 and 2 ([l][j] blocks like rtab, which then holds
-    // pass 3), and two per-view volume buffers of the passes (chunk views each)
+    // three-pass rotation (rot3.cu): the 4-tap table of passes 1 + 2 ([l][j]
+    // blocks of rot3_ts4(nx) floats), the table of the transposed pass 3 (like
+    // rtab, which then holds pass 3), and two per-view volume buffers
     int rot3 = 0;
-    float* r3_p1 = nullptr;
-    float* r3_p2 = nullptr;
+    float* r3_p12 = nullptr;
     float* r3_t3 = nullptr;
-    float* r3_t2 = nullptr;
     float* r3_a = nullptr;
     float* r3_b = nullptr;
     size_t r3_cap = 0;           // floats of each of r3_a, r3_b
@@ -375,6 +373,7 @@ cudaError_t launch_rot_tables(const spect_plan_s& P, cudaStream_t st);
 cudaError_t launch_fused_forward(const spect_plan_s& P, const float* xt, int l0, int nv, cudaStream_t st);
 cudaError_t launch_fused_rotate(const spect_plan_s& P, const float* xt, int l0, int nv, cudaStream_t st);
 // three-pass rotation (rot3.cu)
+int rot3_ts4(int nx);
 cudaError_t build_rot3(spect_plan_s& P, const double* angles, const float* mu_t, cudaStream_t st);
 cudaError_t launch_rot3_forward_passes(const spect_plan_s& P, const float* xt, int l0, int nv, cudaStream_t st);
 cudaError_t launch_rot3_adjoint_passes(const spect_plan_s& P, int l0, int nv, cudaStream_t st);
