@@ -92,9 +92,9 @@ enum {
      * exact transpose (the passes' transposes in reverse order).  Fused
      * plans only: with SPECT_PLAN_LOW_MEMORY, or when the fused kernels do
      * not fit the geometry, spect_plan_create returns SPECT_EUNSUPPORTED.
-     * The plan holds two more rotation tables (nview*ny*(13nx) floats) and
-     * two per-view pass buffers (2 * chunk views * ny*(nx*nz rounded up to
-     * 4) floats). */
+     * The three passes run as one eight-tap gather per output inside the
+     * rotation kernel (table: nview*ny*16nx floats) and as eight-entry
+     * adjacency lists in A'. */
     SPECT_PLAN_ROTATION_3PASS = 1u << 2
 };
 

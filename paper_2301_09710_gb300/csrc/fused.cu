@@ -381,7 +381,7 @@ constexpr int kRotThreads = 512;
 // instead of as per-element global loads, when the two planes fit.
 template <int P, bool MUS>
 __global__ void __launch_bounds__(kRotThreads, 2) k_rot_fwd(Geometry g, FusedDims d, const float* __restrict__ rtab,
-                                                         const float* __restrict__ xt, size_t xt_vs,
+                                                         const float* __restrict__ xt,
                                                          const float* __restrict__ mubar, float* __restrict__ wsl,
                                                          int l0, int* err)
 {
@@ -397,7 +397,6 @@ __global__ void __launch_bounds__(kRotThreads, 2) k_rot_fwd(Geometry g, FusedDim
     const int j = blockIdx.x, v = blockIdx.y, l = l0 + v;
     const int pln = nx * nz;
     const int wp = d.wpf;
-    xt += (size_t)v * xt_vs;  // per-view input volumes (the three-pass rotation), else one
     const int wcols = d.nib * Sep<P>::CX + 2 * C;
     const float* tab = rtab + ((size_t)l * ny + j) * d.ts;
     const float* mb = mubar + ((size_t)l * ny + j) * d.ps;
@@ -501,6 +500,113 @@ __global__ void __launch_bounds__(kRotThreads, 2) k_rot_fwd(Geometry g, FusedDim
     }
     // tile images: row k of tile t is W[k][t*TI .. t*TI + TI + 2C), cut at
     // the end of the plane's row (the blur never reads past it)
+    for (int r = warp; r < d.nT * nz; r += NW) {
+        const int t = r / nz, k = r - t * nz;
+        const int tw = min(d.TI + 2 * C, wcols - t * d.TI);
+        const float* src = S + k * wp + t * d.TI;
+        float* out = dst + (size_t)t * d.warea + (size_t)k * d.wp;
+        for (int c = lane; c < tw; c += 32) out[c] = src[c];
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Forward rotation with the three-pass rotation (rot3.cu): the same block, plane
+// image, attenuation and output as k_rot_fwd, but every output (i, k) of plane
+// j is the eight-tap sum  sum_m w_m x_t[off_m + k]  of its table row (the three
+// passes' products; unused taps have weight 0, offset 0).  The (view, row)
+// table -- nx x 8 weights, then nx x 8 offsets -- is staged in shared memory
+// once; warps take one row i per step with lanes over k (24 gathers in
+// flight per lane, as k_rot_fwd's row pairs).
+// ----------------------------------------------------------------------------
+template <int P, bool MUS>
+__global__ void __launch_bounds__(kRotThreads, 2) k_rot_fwd8(Geometry g, FusedDims d, const float* __restrict__ tab8,
+                                                          const float* __restrict__ xt,
+                                                          const float* __restrict__ mubar, float* __restrict__ wsl,
+                                                          int l0, int* err)
+{
+    constexpr int C = Sep<P>::C;
+    extern __shared__ __align__(16) float sm[];
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int ts8 = 16 * nx;
+    float* S = sm;
+    float* TBL = sm + d.farea;  // nx x 8 weights, then nx x 8 int offsets
+    float* MU = TBL + ts8;      // [i][k] attenuation plane (MUS)
+    uint64_t* bar = reinterpret_cast<uint64_t*>(MU + d.ps);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = kRotThreads / 32;
+    const int j = blockIdx.x, v = blockIdx.y, l = l0 + v;
+    const int wp = d.wpf;
+    const int wcols = d.nib * Sep<P>::CX + 2 * C;
+    const float* tab = tab8 + ((size_t)l * ny + j) * ts8;
+    const float* mb = mubar + ((size_t)l * ny + j) * d.ps;
+    if (MUS && threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tma_load_1d(MU, mb, (unsigned)d.ps * 4u, bar);
+    }
+    for (int e = threadIdx.x; e < ts8 / 4; e += kRotThreads)
+        reinterpret_cast<float4*>(TBL)[e] = __ldg(reinterpret_cast<const float4*>(tab) + e);
+    __syncthreads();  // table staged; the barrier is initialised before anyone waits on it
+    const int* OFF = reinterpret_cast<const int*>(TBL + 8 * nx);
+    bool ok = true, waited = !MUS;
+
+    for (int i = warp; i < nx; i += NW) {
+        const float4 wl = reinterpret_cast<const float4*>(TBL)[2 * i];
+        const float4 wh = reinterpret_cast<const float4*>(TBL)[2 * i + 1];
+        const int4 ol = reinterpret_cast<const int4*>(OFF)[2 * i];
+        const int4 oh = reinterpret_cast<const int4*>(OFF)[2 * i + 1];
+        const float w[8] = {wl.x, wl.y, wl.z, wl.w, wh.x, wh.y, wh.z, wh.w};
+        const int o[8] = {ol.x, ol.y, ol.z, ol.w, oh.x, oh.y, oh.z, oh.w};
+        for (int k0 = 0; k0 < nz; k0 += 96) {
+            float xs[3][8], ma[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int k = k0 + 32 * q + lane;
+                if (k < nz) {
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) xs[q][m] = __ldg(xt + o[m] + k);
+                    if (!MUS) ma[q] = __ldg(mb + i * nz + k);
+                }
+            }
+            if (!waited) {
+                ok = mbar_wait_bounded(bar, 0u);
+                waited = true;
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int k = k0 + 32 * q + lane;
+                if (k < nz) {
+                    if (MUS) ma[q] = MU[i * nz + k];
+                    float* wr = S + k * wp + C;
+                    float va = w[0] * xs[q][0];
+#pragma unroll
+                    for (int m = 1; m < 8; ++m) va = fmaf(w[m], xs[q][m], va);
+                    va *= ma[q];
+                    wr[i] = va;
+                    if (i == 0)  // replicate padding along i: left halo columns
+                        for (int h = -C; h < 0; ++h) wr[h] = va;
+                    if (i == nx - 1)  // right halo columns
+                        for (int h = nx; h < wcols - C; ++h) wr[h] = va;
+                }
+            }
+        }
+    }
+    if (__syncthreads_or(!ok)) {  // the attenuation plane never arrived
+        if (threadIdx.x == 0) {
+            flag_timeout(err);
+            mbar_wait_bounded(bar, 0u);  // a last chance for the copy in flight to land
+        }
+        return;
+    }
+    float* dst = wsl + ((size_t)v * ny + j) * d.parea;
+    if (d.nT == 1) {
+        if (threadIdx.x == 0) {
+            fence_proxy_async_smem();
+            tma_store_1d(dst, S, (unsigned)d.parea * 4u);
+            tma_store_wait_read<0>();  // the block may leave once its shared memory is read
+        }
+        return;
+    }
     for (int r = warp; r < d.nT * nz; r += NW) {
         const int t = r / nz, k = r - t * nz;
         const int tw = min(d.TI + 2 * C, wcols - t * d.TI);
@@ -1336,15 +1442,17 @@ template <int P>
 cudaError_t rot_launch(const spect_plan_s& Pl, const float* xt, int l0, int nv, cudaStream_t st)
 {
     const FusedDims d = dims_for<P>(Pl.g, Pl.fused_J, Pl.fused_nT);
-    const size_t smem_mu = rot_smem_min(d) + (size_t)d.ps * sizeof(float) + 16;
+    // the three-pass rotation: eight taps per output from its own table
+    const size_t smin = Pl.rot3 ? ((size_t)d.farea + (size_t)rot3_ts8(Pl.g.nx)) * sizeof(float) : rot_smem_min(d);
+    const size_t smem_mu = smin + (size_t)d.ps * sizeof(float) + 16;
     const bool mus = smem_mu <= (size_t)Pl.smem_optin;
-    const size_t smem = mus ? smem_mu : rot_smem_min(d);
-    auto kern = mus ? k_rot_fwd<P, true> : k_rot_fwd<P, false>;
+    const size_t smem = mus ? smem_mu : smin;
+    auto kern = Pl.rot3 ? (mus ? k_rot_fwd8<P, true> : k_rot_fwd8<P, false>)
+                        : (mus ? k_rot_fwd<P, true> : k_rot_fwd<P, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    // the three-pass rotation hands each view its own pass-2 volume
-    const size_t xvs = Pl.rot3 ? (size_t)Pl.g.nx * Pl.g.ny * Pl.g.nz : 0;
-    kern<<<dim3(Pl.g.ny, nv), kRotThreads, smem, st>>>(Pl.g, d, Pl.rtab, xt, xvs, Pl.mubar, Pl.slab, l0, Pl.err);
+    kern<<<dim3(Pl.g.ny, nv), kRotThreads, smem, st>>>(Pl.g, d, Pl.rot3 ? Pl.r3_tab : Pl.rtab, xt, Pl.mubar,
+                                                       Pl.slab, l0, Pl.err);
     return cudaGetLastError();
 }
 
@@ -1570,8 +1678,7 @@ cudaError_t launch_adj_rot_t(const spect_plan_s& P, int l0, int nv, float* out, 
     const bool vec4 = (P.g.nz % 4) == 0;
     const size_t n = (size_t)P.g.nx * P.g.ny * (vec4 ? P.g.nz / 4 : P.g.nz);
     const unsigned blocks = (unsigned)((n + 255) / 256);
-    // the three-pass rotation's lists read the output of its transposed pass 3
-    const float* src = P.rot3 ? P.r3_a : P.slab;
+    const float* src = P.slab;
     switch (P.adj_max) {
 #define SPECT_ADJ(M)                                                                                                 \
     case M:                                                                                                          \

@@ -134,7 +134,7 @@ void free_plan(spect_plan_s* P, cudaStream_t st)
     for (cudaEvent_t e : P->evpool) cudaEventDestroy(e);
     void* ptrs[] = {P->mu, P->psf, P->psf_adj, P->fx, P->fz, P->fx_adj, P->fz_adj, P->rot, P->adj_off, P->adj,
                     P->slab, P->e, P->ratio, P->s, P->mubar, P->xt, P->et, P->st, P->part, P->adjf, P->err, P->rtab, P->ut,
-                    P->gboxes, P->gent, P->rboxes, P->r3_p12, P->r3_t3, P->r3_a, P->r3_b};
+                    P->gboxes, P->gent, P->rboxes, P->r3_tab};
     for (void* p : ptrs) raw_free(P, p, st);
     delete P;
 }
@@ -253,13 +253,8 @@ spect_status fast_forward(spect_plan_s* P, const float* xt, float* v, const floa
     const int nview = P->g.nview;
     for (int l0 = 0; l0 < nview; l0 += P->chunk) {
         const int nv = std::min(P->chunk, nview - l0);
-        if (P->rot3) {  // passes 1 and 2 of the three-pass rotation; pass 3 is the rotation kernel
-            SPECT_CUDA_TRY(counted(P, SPECT_K_ROTATE_ATTEN, st,
-                                   [&] { return spect::launch_rot3_forward_passes(*P, xt, l0, nv, st); }),
-                           "three-pass rotation launch");
-        }
         SPECT_CUDA_TRY(counted(P, SPECT_K_ROTATE_ATTEN, st,
-                               [&] { return spect::launch_fused_rotate(*P, P->rot3 ? P->r3_b : xt, l0, nv, st); }),
+                               [&] { return spect::launch_fused_rotate(*P, xt, l0, nv, st); }),
                        "rotation launch");
         SPECT_CUDA_TRY(counted(P, SPECT_K_CONV_FWD, st,
                                [&] { return spect::launch_fused_forward(*P, xt, l0, nv, st); }),
@@ -279,10 +274,6 @@ spect_status fast_back(spect_plan_s* P, const float* v, float* out_t, spect::EmA
         const bool last = l0 + nv >= nview;
         SPECT_CUDA_TRY(counted(P, SPECT_K_CONV_ADJ, st, [&] { return spect::launch_fused_adjoint(*P, v, l0, nv, st); }),
                        "fused adjoint launch");
-        if (P->rot3)  // transposed passes 3 and 2; the list gather does the transposed pass 1
-            SPECT_CUDA_TRY(counted(P, SPECT_K_ROTATE_ADJ, st,
-                                   [&] { return spect::launch_rot3_adjoint_passes(*P, l0, nv, st); }),
-                           "three-pass adjoint rotation launch");
         spect::EmArgs e = em;
         if (!last) e.x = nullptr;
         SPECT_CUDA_TRY(counted(P, SPECT_K_ROTATE_ADJ, st,
@@ -368,8 +359,8 @@ size_t plan_bytes_bound(const spect_plan_s& P)
         // patch gather: boxes and box-local entries (at most 8 per list)
         const size_t np = (size_t)((g.nx + 7) / 8) * ((g.ny + 7) / 8) * g.nview;
         b += np * 16 + np * 64 * 8 * sizeof(spect::AdjEntry) + np * 16;  // + rotation boxes
-        if (P.rot3)  // two more tables and two per-view pass buffers
-            b += (size_t)g.nview * g.ny * (8 * (size_t)g.nx + P.ts) * F + 2 * (size_t)g.ny * P.ps * chunk * F;
+        if (P.rot3)  // the eight-tap table
+            b += (size_t)g.nview * g.ny * 16 * (size_t)g.nx * F;
     }
     return b;
 }
@@ -575,9 +566,9 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
         PLAN_TRY(e2, "adjacency counts download");
         PLAN_TRY(e3, "adjacency max download");
         PLAN_TRY(e4, "adjacency count");
-        if (P->rot3) mx = std::max(mx, 4);  // four entries per (voxel, view) for the three-pass lists
+        if (P->rot3) mx = std::max(mx, 8);  // eight entries per (voxel, view) for the three-pass lists
         P->adj_max = mx;
-        if (P->fast && mx > 8 && !P->rot3) P->fast = 0;  // fixed-length lists are instantiated up to 8 entries
+        if (P->fast && mx > 8) P->fast = 0;  // fixed-length lists are instantiated up to 8 entries
         if (P->fast) {
             PLAN_ALLOC(P->adjf, nlist * (size_t)std::max(mx, 1), "adjacency lists");
             if (mx < 1) P->adj_max = 1;
@@ -636,20 +627,20 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
         P->part_cap = nproj * (size_t)spect::fused_groups(*P);
         // mu in the [j][i][k] layout (temporary, the slab serves as scratch)
         PLAN_TRY(spect::launch_transpose(P->mu, P->slab, nz, (int)nxy, st), "mu transpose launch");
-        PLAN_ALLOC(P->rtab, (size_t)nview * ny * P->ts, "rotation tables");
         if (P->rot3) {
-            // three passes: the 4-tap table of passes 1 + 2, the table of the
-            // transposed pass 3 (rtab holds pass 3), per-view pass buffers, the lists
-            // of the transposed passes 2 and 1 (in adjf), and the attenuation cache
-            // from mu turned the same way
-            PLAN_ALLOC(P->r3_p12, (size_t)nview * ny * spect::rot3_ts4(nx), "three-pass tables");
-            PLAN_ALLOC(P->r3_t3, (size_t)nview * ny * P->ts, "three-pass tables");
-            P->r3_cap = (size_t)ny * P->ps * P->chunk;
-            PLAN_ALLOC(P->r3_a, P->r3_cap, "three-pass buffers");
-            PLAN_ALLOC(P->r3_b, P->r3_cap, "three-pass buffers");
-            PLAN_TRY(spect::build_rot3(*P, angles, P->slab, st), "three-pass rotation set-up");
+            // three passes: the eight-tap table of the forward rotation kernel, the
+            // eight-entry lists of the adjoint gather (in adjf), and the attenuation
+            // cache from mu turned the same way (one volume of scratch)
+            PLAN_ALLOC(P->r3_tab, (size_t)nview * ny * spect::rot3_ts8(nx), "three-pass table");
+            float* scratch = nullptr;
+            PLAN_TRY(raw_alloc(P, (void**)&scratch, vol * sizeof(float), st), "three-pass scratch");
+            cudaError_t e3 = spect::build_rot3(*P, angles, P->slab, scratch, st);
+            raw_free(P, scratch, st);
+            PLAN_TRY(e3, "three-pass rotation set-up");
+            PLAN_TRY(spect::build_gather(*P, st), "patch gather set-up");  // boxes of the three-pass lists
         } else {
             PLAN_TRY(spect::launch_mubar_cache(*P, P->slab, st), "attenuation cache launch");
+            PLAN_ALLOC(P->rtab, (size_t)nview * ny * P->ts, "rotation tables");
             PLAN_TRY(spect::launch_rot_tables(*P, st), "rotation table launch");
             PLAN_TRY(spect::build_gather(*P, st), "patch gather set-up");
             PLAN_TRY(spect::build_rotpatch(*P, st), "patch rotation set-up");
@@ -958,13 +949,6 @@ spect_status reconfigure(spect_plan_s* P, int J, int adj_J, int tiles, cudaStrea
         P->adj_J = oaJ;
         P->fused_nT = ont;
         return r;
-    }
-    if (P->rot3) {  // the pass buffers hold the chunk's views
-        const size_t need = (size_t)g.ny * P->ps * chunk;
-        size_t cap_b = P->r3_cap;  // r3_cap grows only once both buffers have
-        r = realloc_floats(P, &P->r3_b, &cap_b, need, st, "three-pass buffers");
-        if (r == SPECT_OK) r = realloc_floats(P, &P->r3_a, &P->r3_cap, need, st, "three-pass buffers");
-        if (r != SPECT_OK) return r;
     }
     P->chunk = chunk;
     P->adj_chunk = P->adj_chunk_req > 0 ? std::min(P->adj_chunk_req, chunk) : chunk;

@@ -103,15 +103,11 @@ struct spect_plan_s {
     // used instead of k_rot_fwd when rotpatch_on != 0 (chosen by the autotuner)
     int rotpatch = 0;
     int rotpatch_on = 0;
-    // three-pass rotation (rot3.cu): the 4-tap table of passes 1 + 2 ([l][j]
-    // blocks of rot3_ts4(nx) floats), the table of the transposed pass 3 (like
-    // rtab, which then holds pass 3), and two per-view volume buffers
+    // three-pass rotation (rot3.cu): the eight-tap table of the forward
+    // rotation, [l][j] blocks of rot3_ts8(nx) floats (the adjoint's lists
+    // are in adjf)
     int rot3 = 0;
-    float* r3_p12 = nullptr;
-    float* r3_t3 = nullptr;
-    float* r3_a = nullptr;
-    float* r3_b = nullptr;
-    size_t r3_cap = 0;           // floats of each of r3_a, r3_b
+    float* r3_tab = nullptr;
     int4* rboxes = nullptr;      // [patch][l] source box of x_t (i0, j0, width, height)
     int rbw = 0, rbh = 0;
     CUtensorMap rmap_x, rmap_mu; // x_t (k, i, j) and the attenuation cache (k, i, plane)
@@ -372,11 +368,10 @@ cudaError_t launch_build_adjacency_fixed(const spect_plan_s& P, cudaStream_t st)
 cudaError_t launch_rot_tables(const spect_plan_s& P, cudaStream_t st);
 cudaError_t launch_fused_forward(const spect_plan_s& P, const float* xt, int l0, int nv, cudaStream_t st);
 cudaError_t launch_fused_rotate(const spect_plan_s& P, const float* xt, int l0, int nv, cudaStream_t st);
-// three-pass rotation (rot3.cu)
-int rot3_ts4(int nx);
-cudaError_t build_rot3(spect_plan_s& P, const double* angles, const float* mu_t, cudaStream_t st);
-cudaError_t launch_rot3_forward_passes(const spect_plan_s& P, const float* xt, int l0, int nv, cudaStream_t st);
-cudaError_t launch_rot3_adjoint_passes(const spect_plan_s& P, int l0, int nv, cudaStream_t st);
+// three-pass rotation (rot3.cu): table block size, and the plan-time build of
+// the table, the adjoint lists (adjf, adj_max >= 8) and the attenuation cache
+int rot3_ts8(int nx);
+cudaError_t build_rot3(spect_plan_s& P, const double* angles, const float* mu_t, float* scratch, cudaStream_t st);
 size_t fused_slab_per_view(const spect_plan_s& P);
 cudaError_t launch_fused_adjoint(const spect_plan_s& P, const float* v, int l0, int nv, cudaStream_t st);
 cudaError_t launch_fwd_reduce(const spect_plan_s& P, float* v, const float* em_y, const float* em_rbar,

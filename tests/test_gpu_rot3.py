@@ -107,3 +107,29 @@ def test_rot3_config2_sampled_views():
                  what="A' y sampled views (3-pass)")
     plan.check()
     plan.close()
+
+
+@pytest.mark.parametrize("case", [(33, 12, 9, 5, 61), (64, 16, 24, 37, 62)], ids=["33x12", "64x16"])
+def test_rot3_patch_gather_bitwise_equals_list_gather(case, monkeypatch):
+    """The patch gather stages boxes of the transposed pass-3 output and sums the
+    four-entry lists in their order: A' and the EM update are bitwise those of the
+    list gather."""
+    nx, nz, nview, p, seed = case
+    prob = synthetic.random_problem(seed, nx=nx, nz=nz, nview=nview, px=p, pz=p, mu_scale=0.1)
+    ang = np.random.default_rng(seed).uniform(0, 2 * np.pi, nview)
+    plan = _plan(prob, ang, "fused")
+    monkeypatch.setenv("SPECT_GATHER", "0")
+    ref = _plan(prob, ang, "fused")
+    monkeypatch.delenv("SPECT_GATHER")
+    assert plan.info()["device_bytes"] > ref.info()["device_bytes"]  # the patch boxes and entries
+    yy = dev(np.random.default_rng(seed).uniform(0, 1, plan.proj_shape))
+    assert np.array_equal(host(plan.back(yy)), host(ref.back(yy)))
+    y = synthetic.poisson_counts(oracle.forward(prob.x, prob.mu, oracle_psf(prob, "fused"), prob.dy, ang,
+                                                rotation="3pass") * 20, seed)
+    x0 = np.full(prob.x.shape, 0.5, np.float32)
+    xa, xr = dev(x0), dev(x0)
+    plan.em_step(xa, dev(y), None, niter=2)
+    ref.em_step(xr, dev(y), None, niter=2)
+    assert np.array_equal(host(xa), host(xr))
+    plan.check()
+    ref.check()
