@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--direct-steps", type=int, default=3, help="steps of the full-PSF path reported beside (0: skip)")
     ap.add_argument("--rot3-steps", type=int, default=20,
                     help="steps with the three-pass rotation reported beside (0: skip)")
+    ap.add_argument("--rotation", choices=["bilinear", "3pass"], default="bilinear",
+                    help="image rotation of the timed path (Section II-A implements both)")
     ap.add_argument("--cpu-views", type=int, default=0, help="views in the CPU baseline sample (0: auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default launch shapes")
@@ -133,7 +135,8 @@ def make_workload(device, path, nview=NVIEW, autotune=True, rotation="bilinear")
         if autotune:
             plan.autotune()  # the library's launch-shape autotuner (timed on this device, outside the timed region)
     else:
-        plan = SpectPlan(NX, NZ, nview, mu=prob.mu, dy=prob.dy, psf=prob.full_psf(), device=device)
+        plan = SpectPlan(NX, NZ, nview, mu=prob.mu, dy=prob.dy, psf=prob.full_psf(), device=device,
+                         rotation=rotation)
     xt = torch.from_numpy(prob.x).to(device)
     primary = plan.forward(xt)
     scale = 1e7 / float(primary.sum())
@@ -204,7 +207,8 @@ def run_ours(args):
     from __graft_entry__ import build
     build()
 
-    prob, plan, x0_h, y_h, rbar_h = make_workload(device, args.path, args.nview, autotune=not args.no_autotune)
+    prob, plan, x0_h, y_h, rbar_h = make_workload(device, args.path, args.nview, autotune=not args.no_autotune,
+                                                  rotation=args.rotation)
     info = plan.info()
     launch_shape = plan.tuning if info["fused"] else None
     sep = info["separable"]
@@ -369,7 +373,7 @@ def run_ours(args):
                   "gflop_per_pair": 2 * algorithmic_flops("conv_fwd", NVIEW, False) / 1e9,
                   "note": "same workload with the full 37x37 PSF stack (direct 2D blur, no separability)"}
         dplan.close()
-    if args.rot3_steps > 0 and args.path == "separable" and args.nview == NVIEW:
+    if args.rot3_steps > 0 and args.path == "separable" and args.nview == NVIEW and args.rotation == "bilinear":
         _, rplan, _, _, _ = make_workload(device, "separable", rotation="3pass")
         rms = side_ms(rplan, args.rot3_steps)
         rot3 = {"value": 1e3 / rms, "unit": UNIT, "ms_per_step": rms, "launch_shape": rplan.tuning,
@@ -388,7 +392,8 @@ def run_ours(args):
                "config": {"workload": "128x128x80 image, 128 views over 360 deg, 37x37 depth-dependent "
                                       "anisotropic Gaussian PSF (separable factors), MLEM step with 10% smoothed "
                                       "background, XCAT-like ellipsoid phantom (seed 0)",
-                          "path": args.path, "fused": info["fused"], "view_chunk": chunk, "nview": args.nview, "parallelism": f"replicas{world}",
+                          "path": args.path, "rotation": args.rotation, "fused": info["fused"], "view_chunk": chunk,
+                          "nview": args.nview, "parallelism": f"replicas{world}",
                           "launch_shape": launch_shape,
                           "l2": "flushed between timed steps (256 MB write)",
                           "step": "one EM iteration = one A + one A' + fused ratio/update"},
