@@ -133,3 +133,31 @@ def test_rot3_patch_gather_bitwise_equals_list_gather(case, monkeypatch):
     assert np.array_equal(host(xa), host(xr))
     plan.check()
     ref.check()
+
+
+@pytest.mark.parametrize("case", [(48, 20, 6, 11, 9, 1, 63, 3), (37, 13, 9, 5, 9, 9, 64, 2)],
+                         ids=["48x20t3", "37x13t2vpsf"])
+def test_rot3_column_tiled_and_view_dependent_psf(case, monkeypatch):
+    """Column-tiled planes (the eight-tap rotation kernel's tile-image output) and
+    a view-dependent PSF: parity with the oracle, and tiled A x bitwise equal to
+    untiled."""
+    nx, nz, nview, px, pz, nvp, seed, tiles = case
+    prob = synthetic.random_problem(seed, nx=nx, nz=nz, nview=nview, px=px, pz=pz, nview_psf=nvp, mu_scale=0.1)
+    rng = np.random.default_rng(seed)
+    ang = rng.uniform(0, 2 * np.pi, nview)
+    psf = oracle_psf(prob, "fused")
+    untiled = _plan(prob, ang, "fused")
+    monkeypatch.setenv("SPECT_FUSED_TILES", str(tiles))
+    plan = _plan(prob, ang, "fused")
+    monkeypatch.delenv("SPECT_FUSED_TILES")
+    assert plan.tuning["tiles"] > 1
+    x = dev(prob.x)
+    v = host(plan.forward(x))
+    assert_close(v, oracle.forward(prob.x, prob.mu, psf, prob.dy, ang, rotation="3pass"), what="A x (3-pass, tiled)")
+    assert np.array_equal(v, host(untiled.forward(x)))
+    yy = rng.uniform(0, 1, plan.proj_shape).astype(np.float32)
+    xb = host(plan.back(dev(yy)))
+    assert_close(xb, oracle.back(yy, prob.mu, psf, prob.dy, ang, rotation="3pass"), what="A' y (3-pass, tiled)")
+    assert np.array_equal(xb, host(untiled.back(dev(yy))))
+    plan.check()
+    untiled.check()
