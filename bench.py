@@ -421,9 +421,17 @@ def cpu_baseline(args, prob, x0, y, rbar, budget_views=None):
     t0 = time.perf_counter()
     oracle.em_step(x0, y[views], rbar[views], prob.mu, psf, prob.dy, ang, s=s, nthreads=nth)
     dt = time.perf_counter() - t0
+    # the same on one thread, over one view (the oracle's parallel axis is the views)
+    s1 = oracle.sensitivity(prob.mu, psf, prob.dy, ang[:1], nthreads=1)
+    t1 = time.perf_counter()
+    oracle.em_step(x0, y[views[:1]], rbar[views[:1]], prob.mu, psf, prob.dy, ang[:1], s=s1, nthreads=1)
+    dt1 = time.perf_counter() - t1
     return {"value": (nsub / NVIEW) / dt, "unit": UNIT, "cores": nth, "kind": "oracle",
             "sample": f"one FP64 EM step (A + A' over {nsub} of 128 views, full 128x128x80 volume, 37x37 PSF); "
-                      f"{dt:.1f} s, scaled by {nsub}/128", "cpu": cpu_name()}
+                      f"{dt:.1f} s, scaled by {nsub}/128", "cpu": cpu_name(),
+            "single_thread": {"value": (1 / NVIEW) / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"one FP64 EM step over 1 of 128 views on one thread; {dt1:.1f} s, "
+                                        f"scaled by 1/128"}}
 
 
 def cpu_name():
