@@ -10,6 +10,8 @@ a wrong padding rule in the oracle fails at least one of them:
   attenuation   -> closed form for a uniform map, Eq. (1)
   PSF blur      -> scipy.ndimage.convolve(mode="nearest") and a hand-worked
                    1D example (tests/golden/conv_replicate_1d.txt)
+  PSF factors   -> the outer product written index by index, and a blur with
+                   the built stack == scipy convolve1d along i, then along k
   forward A     -> composition of the library routines above (Algorithm 1),
                    line sums for a delta PSF without attenuation
   back A'       -> dense-matrix transpose of A (the paper's Section III-A
@@ -109,6 +111,45 @@ def test_conv_psf_wider_than_plane_matches_scipy():
     w = rng.uniform(0, 1, (3, 4))
     p = rng.uniform(0, 1, (9, 11))
     np.testing.assert_allclose(oracle.conv_plane(w, p), ndimage.convolve(w, p, mode="nearest"), rtol=1e-13)
+
+
+def _asymmetric_factors(rng, nvp, ny, px, pz):
+    """Separable factors with no symmetry, px != pz, different per depth and view."""
+    fx = rng.uniform(0.1, 1.0, (nvp, ny, px)) * np.linspace(1.0, 2.0, px)
+    fz = rng.uniform(0.1, 1.0, (nvp, ny, pz)) * np.linspace(2.0, 0.5, pz)
+    return fx.astype(np.float32), fz.astype(np.float32)
+
+
+def test_psf_from_factors_is_the_outer_product_by_index():
+    """p(a,b,j,l) = fx(a,j,l) fz(b,j,l), written out index by index: a swap of the
+    factors, of a and b, or of the depth / view axes changes the stack."""
+    rng = np.random.default_rng(21)
+    nvp, ny, px, pz = 3, 4, 5, 3
+    fx, fz = _asymmetric_factors(rng, nvp, ny, px, pz)
+    got = oracle.psf_from_factors(fx, fz)
+    assert got.shape == (nvp, ny, pz, px)
+    for l in range(nvp):
+        for j in range(ny):
+            for b in range(pz):
+                for a in range(px):
+                    assert got[l, j, b, a] == np.float64(fx[l, j, a]) * np.float64(fz[l, j, b])
+
+
+def test_psf_from_factors_blur_equals_two_1d_convolutions():
+    """A blur with the stack built from (fx, fz) equals scipy's 1D replicate-padded
+    convolution along i with fx followed by the one along k with fz (Section II-A:
+    replicate padding acts on each axis on its own, so the separable blur
+    factorises), for every depth and view of the stack."""
+    rng = np.random.default_rng(22)
+    nvp, ny, px, pz = 2, 3, 7, 5
+    fx, fz = _asymmetric_factors(rng, nvp, ny, px, pz)
+    psf = oracle.psf_from_factors(fx, fz)
+    w = rng.uniform(0, 1, (9, 11))  # (nz, nx)
+    for l in range(nvp):
+        for j in range(ny):
+            u = ndimage.convolve1d(w, fx[l, j].astype(np.float64), axis=1, mode="nearest")
+            want = ndimage.convolve1d(u, fz[l, j].astype(np.float64), axis=0, mode="nearest")
+            np.testing.assert_allclose(oracle.conv_plane(w, psf[l, j]), want, rtol=1e-13, atol=0)
 
 
 def _golden_conv():
