@@ -165,7 +165,8 @@ def algorithmic_flops(kind: str, nv: float, sep: bool, fused: bool = False) -> f
 
 
 # DRAM bytes (read + write) per 128-view launch of the fused separable kernels, from one ncu capture of the
-# 32-view case scaled by 4 (profiles/fused_kernels_128x128x80_32views.md); valid for the kernels as captured.
+# same kernels on the 32-view case of this workload, scaled by 4 (traffic grows with the views); valid for the
+# kernels as captured.
 NCU_TRAFFIC_BYTES_128 = {"conv_adj": 1156.6e6, "conv_fwd": 890.8e6, "rotate_atten": 1402.9e6, "rotate_adj": 1108.6e6}
 
 
@@ -458,7 +459,8 @@ def run_reference(args):
     oracle.build()
     prob = synthetic.config2(seed=0, nx=NX, nz=NZ, nview=NVIEW, psf_size=PSF)
     nth = oracle.max_threads()
-    nsub = args.cpu_views or max(2, min(8, nth // 2))
+    # the oracle parallelises over views (one OpenMP thread per view): one view per host thread keeps every core busy
+    nsub = args.cpu_views or max(2, min(NVIEW, nth))
     views = np.linspace(0, NVIEW, nsub, endpoint=False).astype(int)
     ang = oracle.default_angles(NVIEW)[views]
     psf = oracle.psf_from_factors(prob.fx, prob.fz)
@@ -483,7 +485,10 @@ def run_reference(args):
     value = done * (nsub / NVIEW) / dt
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": done,
-        "steps_requested": args.steps, "warmup": args.warmup, "ms_per_step": dt / done * 1e3 * NVIEW / nsub,
+        "steps_requested": args.steps, "warmup": args.warmup,
+        # measured wall time of one timed step (an EM step over the view sample); the time one full 128-view
+        # pair would take at this rate is reported beside it, not as the step time
+        "ms_per_step": dt / done * 1e3, "extrapolated_ms_per_pair": dt / done * 1e3 * NVIEW / nsub,
         "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "128x128x80 image, 128 views, 37x37 PSF, MLEM step (oracle on a view sample)"},

@@ -345,9 +345,10 @@ spect_status spect_batch_destroy(spect_batch batch);
 /*
  * spect_forward_static -- v = A x without any device allocation.
  *
- * For callers that cannot allocate device memory (code running while a CUDA
- * graph is captured, hosts whose device memory is reserved up front, plug-in
- * environments that own the allocator).  No plan is needed: the call takes
+ * For callers that cannot allocate device memory: hosts whose device memory
+ * is reserved up front and may not grow while they run, and plug-in
+ * environments that hand out device buffers but own the allocator, so a
+ * library may not take memory behind their back.  No plan is needed: the call takes
  * the same inputs as spect_plan_create (separable PSF factors only) plus x and
  * v, and uses a work slab and rotation constants held in fixed-size static
  * device arrays of the library (the paper has no counterpart).  Nothing is
@@ -358,8 +359,8 @@ spect_status spect_batch_destroy(spect_batch batch);
  * Limits: nx*ny*nz <= 8388608 voxels and nview <= 4096, else SPECT_EINVAL.
  * The static arrays (32 MiB + 64 KiB) are held by every device that loads the
  * library until the process exits.  The first call on a device looks up
- * their device addresses (cudaGetSymbolAddress); make that first call before
- * any stream capture.  All calls share the arrays: calls that overlap on the
+ * their device addresses (cudaGetSymbolAddress), with that device current.
+ * All calls share the arrays: calls that overlap on the
  * GPU (other streams or host threads) race and must be serialised.
  * Errors: SPECT_EINVAL (arguments, sizes beyond the limits), SPECT_EUNSUPPORTED,
  * SPECT_ECUDA.

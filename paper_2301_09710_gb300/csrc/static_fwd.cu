@@ -1,10 +1,11 @@
 // static_fwd.cu -- spect_forward_static: the forward projection v = A x for
 // callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all: code running while a CUDA graph
-// is being captured, real-time or embedded hosts whose memory is reserved up
-// front, and plug-in environments that hand out device buffers but own the
-// allocator.  For them this entry point runs the low-memory separable-PSF
+// Some callers cannot call cudaMalloc at all: real-time or embedded hosts
+// whose device memory is reserved up front and may not grow while they run,
+// and plug-in environments (a host application's image pipeline, say) that
+// hand out device buffers but own the allocator, so a library must not take
+// memory behind their back.  For them this entry point runs the low-memory separable-PSF
 // kernels (rotate + attenuate into a work slab, then blur + depth sum) with
 // the slab and the per-view rotation constants in file-scope __device__
 // arrays of fixed size, instead of a plan.  The caller passes every input and

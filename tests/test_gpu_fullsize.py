@@ -127,3 +127,35 @@ def test_large_planes_sampled_views(shape):
     assert abs(lhs - rhs) <= ADJ_FP32 * abs(lhs)
     plan.check()
     plan.close()
+
+
+def test_benchmark_plan_all_views_vs_oracle(prob):
+    """The benchmark's own problem and launch configuration, element by element:
+    the 128-view plan autotuned as the benchmark tunes it, A x over all 128 views,
+    A' y with y nonzero in every view (the view sum over all 128 views and the
+    depth-group split of the autotuned shape), and one MLEM step with the smoothed
+    10 % background, each against the FP64 oracle on all host threads."""
+    from paper_2301_09710_gb300 import SpectPlan
+    ang = oracle.default_angles(128)
+    nz, ny, nx = prob.x.shape
+    plan = SpectPlan(nx, nz, 128, mu=prob.mu, dy=prob.dy, fx=prob.fx, fz=prob.fz)
+    plan.autotune()
+    assert plan.info()["fused"]
+    psf = oracle.psf_from_factors(prob.fx, prob.fz)
+    v = host(plan.forward(dev(prob.x)))
+    v_o = oracle.forward(prob.x, prob.mu, psf, prob.dy, ang)
+    assert_close(v, v_o, what=f"A x, all 128 views, shape {plan.tuning}")
+    rng = np.random.default_rng(11)
+    y = rng.uniform(0.5, 1.5, plan.proj_shape).astype(np.float32)
+    assert_close(host(plan.back(dev(y))), oracle.back(y, prob.mu, psf, prob.dy, ang),
+                 what=f"A' y, all 128 views, shape {plan.tuning}")
+    scale = 1e7 / v_o.sum()
+    rbar = synthetic.background_from((v_o * scale).astype(np.float32), 0.1, 8.0)
+    yc = synthetic.poisson_counts(v_o * scale + rbar, 0)
+    x0 = np.where(prob.body, 1.0, 0.0).astype(np.float32)
+    xg = dev(x0)
+    plan.em_step(xg, dev(yc), dev(rbar), niter=1)
+    assert_close(host(xg), oracle.em_step(x0, yc, rbar, prob.mu, psf, prob.dy, ang),
+                 what="MLEM step, all 128 views")
+    plan.check()
+    plan.close()

@@ -1,9 +1,10 @@
 """spect_forward_static: the forward projection for callers that cannot
-allocate device memory (graph capture, reserved-memory hosts, plug-ins that own
-the allocator).  Its work slab lives in a fixed-size static device array, so
-it must give the same projections as the plan-based spect_forward, call after
-call.  This file is collected last so that a failure here leaves every other
-test already run.
+allocate device memory (hosts whose device memory is reserved up front,
+plug-ins whose host application owns the allocator).  Its work slab lives in a
+fixed-size static device array shared by every call, so it must give the same
+projections as the plan-based spect_forward, call after call, and those must
+match the FP64 oracle.  This file is collected last so that a failure here
+leaves every other test already run.
 """
 import numpy as np
 import pytest
@@ -27,10 +28,13 @@ def test_static_forward_matches_plan_forward_on_consecutive_calls():
     v_ref = host(plan.forward(x))
     plan.check()
     mu, fx, fz = dev(prob.mu), dev(prob.fx), dev(prob.fz)
+    v_o = oracle.forward(prob.x, prob.mu, oracle.psf_from_factors(prob.fx, prob.fz), prob.dy, ang)
     for _ in range(2):
         out = torch.full(plan.proj_shape, float("nan"), device="cuda")
         forward_static(x, prob.nview, fx, fz, mu=mu, dy=prob.dy, angles=ang, out=out)
-        assert_close(host(out), v_ref, what="static-scratch forward vs plan forward")
+        got = host(out)
+        assert_close(got, v_ref, what="static-scratch forward vs plan forward")
+        assert_close(got, v_o, what="static-scratch forward vs FP64 oracle")
 
 
 def test_static_forward_rejects_volume_beyond_scratch():
