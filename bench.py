@@ -44,11 +44,17 @@ def parse():
     ap.add_argument("--direct-steps", type=int, default=3, help="steps of the full-PSF path reported beside (0: skip)")
     ap.add_argument("--rot3-steps", type=int, default=20,
                     help="steps with the three-pass rotation reported beside (0: skip)")
+    ap.add_argument("--lowmem-steps", type=int, default=5,
+                    help="steps of the O(volume) low-memory plan reported beside (0: skip)")
     ap.add_argument("--rotation", choices=["bilinear", "3pass"], default="bilinear",
                     help="image rotation of the timed path (Section II-A implements both)")
     ap.add_argument("--cpu-views", type=int, default=0, help="views in the CPU baseline sample (0: auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default launch shapes")
+    ap.add_argument("--serve-requests", type=int, default=160,
+                    help="requests of the serving stream (20 req/s) timed served vs one at a time (0: skip)")
+    ap.add_argument("--batch-plans", type=int, default=24,
+                    help="reconstructions of the batching workload timed as one launch vs plan by plan (0: skip)")
     ap.add_argument("--nview", type=int, default=NVIEW,
                     help="views of the workload (default 128; fewer only for small profiler captures)")
     a = ap.parse_args()
@@ -122,7 +128,7 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- workload
-def make_workload(device, path, nview=NVIEW, autotune=True, rotation="bilinear"):
+def make_workload(device, path, nview=NVIEW, autotune=True, rotation="bilinear", low_memory=False):
     import torch
 
     from paper_2301_09710_gb300 import SpectPlan, synthetic
@@ -131,8 +137,8 @@ def make_workload(device, path, nview=NVIEW, autotune=True, rotation="bilinear")
     sep = path == "separable"
     if sep:
         plan = SpectPlan(NX, NZ, nview, mu=prob.mu, dy=prob.dy, fx=prob.fx, fz=prob.fz, device=device,
-                         rotation=rotation)
-        if autotune:
+                         rotation=rotation, low_memory=low_memory)
+        if autotune and not low_memory:
             plan.autotune()  # the library's launch-shape autotuner (timed on this device, outside the timed region)
     else:
         plan = SpectPlan(NX, NZ, nview, mu=prob.mu, dy=prob.dy, psf=prob.full_psf(), device=device,
@@ -364,9 +370,18 @@ def run_ours(args):
         splan.check()
         return sum(dl) / len(dl)
 
-    direct = rot3 = None
-    if args.path == "separable" and (args.direct_steps > 0 or args.rot3_steps > 0):
-        plan.close()
+    direct = rot3 = lowmem = None
+    plan_bytes_main = info["device_bytes"]
+    plan.close()
+    if args.lowmem_steps > 0 and args.path == "separable" and args.rotation == "bilinear":
+        _, lplan, _, _, _ = make_workload(device, "separable", args.nview, low_memory=True)
+        lms = side_ms(lplan, args.lowmem_steps)
+        lowmem = {"value": 1e3 / lms, "unit": UNIT, "ms_per_step": lms,
+                  "plan_bytes": lplan.info()["device_bytes"],
+                  "note": "same workload on a SPECT_PLAN_LOW_MEMORY plan: device memory O(image + projections), "
+                          "the attenuation of Eq. (1) recomputed from the rotated mu-map in every projection "
+                          "(the main line caches it for every view at plan time: plan_bytes there)"}
+        lplan.close()
     if args.direct_steps > 0 and args.path == "separable":
         _, dplan, _, _, _ = make_workload(device, "direct")
         dms = side_ms(dplan, args.direct_steps)
@@ -382,6 +397,18 @@ def run_ours(args):
                         "interpolation along x, y, x) instead of bilinear rotation"}
         rplan.close()
 
+    serving = batching = None
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        serving = serving_line(args.serve_requests, device)
+    if rank == 0 and world == 1 and args.batch_plans > 0:
+        from paper_2301_09710_gb300 import batching as bat
+        b = bat.run(args.batch_plans, niter=8, reps=3)
+        batching = {"workload": b["workload"], "recon_per_s": b["recon_per_s"],
+                    "speedup_vs_plan_by_plan": b["speedup_graph_tuned_vs_plain"],
+                    "bitwise_equal_to_plan_by_plan": b["graph_bitwise_equal_to_plain"],
+                    "kernels_per_launch": b["kernels_per_graph_launch"], "times_s": {
+                        k: b[k] for k in ("plain_s", "graph_s", "plain_tuned_s", "graph_tuned_s")}}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, prob, x0_h, y_h, rbar_h)
@@ -395,11 +422,18 @@ def run_ours(args):
                                       "background, XCAT-like ellipsoid phantom (seed 0)",
                           "path": args.path, "rotation": args.rotation, "fused": info["fused"], "view_chunk": chunk,
                           "nview": args.nview, "parallelism": f"replicas{world}",
-                          "launch_shape": launch_shape,
+                          "launch_shape": launch_shape, "plan_bytes": plan_bytes_main,
+                          "attenuation": "Eq. (1) factors of every view cached at plan time (not in the timed step)",
                           "l2": "flushed between timed steps (256 MB write)",
                           "step": "one EM iteration = one A + one A' + fused ratio/update"},
                "clocks": clk.summary(), "gpu_launches": n_launch, "e2e": e2e, "roofline": roofline,
                "cpu_baseline": cpu, "wall_s_timed_region": wall}
+        if lowmem:
+            out["low_memory_path"] = lowmem
+        if serving:
+            out["serving"] = serving
+        if batching:
+            out["batching"] = batching
         if direct:
             out["direct_path"] = direct
         if rot3:
@@ -408,6 +442,26 @@ def run_ours(args):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def serving_line(n: int, device) -> dict:
+    """Served EM reconstructions against the same requests one at a time: a prefix of n requests of the
+    serving stream (Poisson arrivals at 20 req/s; sizes nx in {64..160}, nz in {32..96}, 60-128 views,
+    PSF 11-37, plus 20 % 192x192x128, 128-view, 37x37-PSF cases; 16-32 MLEM iterations; counts simulated
+    with the library's projector, y ~ Poisson(A x + rbar), 10 % uniform background); admission by the
+    device's free memory; latencies from arrival to the image back on the host."""
+    from paper_2301_09710_gb300 import serving as srv
+    t0 = time.perf_counter()
+    reqs = srv.make_requests(n, 20.0, seed=0, device=device)
+    prep = time.perf_counter() - t0
+    r = srv.compare(reqs)
+    keys = ("recon_per_s", "p50_s", "p95_s", "p99_s", "makespan_s", "peak_active")
+    return {"workload": f"first {n} requests of the 20 req/s serving stream (16-32 MLEM iterations each)",
+            "served": {k: r["served"][k] for k in keys + ("budget_bytes", "held_back_by_free_memory")},
+            "plain": {k: r["plain"][k] for k in keys},
+            "identical_images": r["identical_images"],
+            "p99_ratio_plain_over_served": r["plain"]["p99_s"] / max(r["served"]["p99_s"], 1e-9),
+            "data_prep_s": prep}
 
 
 def cpu_baseline(args, prob, x0, y, rbar, budget_views=None):

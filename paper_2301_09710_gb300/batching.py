@@ -35,15 +35,22 @@ def make_workload(n: int = 24, seed: int = 0, sizes=(64, 96, 128, 160), nzs=(32,
 
 
 def main(argv=None):
-    import torch
-
-    from .projector import SpectBatch, SpectPlan
     ap = argparse.ArgumentParser(description="batched EM reconstructions as one CUDA graph")
     ap.add_argument("--plans", type=int, default=24)
     ap.add_argument("--niter", type=int, default=8)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=0)
     a = ap.parse_args(argv)
+    print(json.dumps(run(a.plans, a.niter, a.reps, a.seed)))
+
+
+def run(n_plans: int = 24, niter: int = 8, reps: int = 3, seed: int = 0) -> dict:
+    """Time the batching workload plan by plan and as one graph launch (default
+    and autotuned launch shapes); returns the figures as a dict."""
+    import torch
+
+    from .projector import SpectBatch, SpectPlan
+    a = argparse.Namespace(plans=n_plans, niter=niter, reps=reps, seed=seed)
     work = make_workload(a.plans, a.seed)
     dev = torch.device("cuda")
     st = torch.cuda.current_stream()
@@ -105,7 +112,9 @@ def main(argv=None):
     for pl in plans:
         pl.check()
     n = len(plans)
-    print(json.dumps({
+    for pl in plans:
+        pl.close()
+    return ({
         "workload": f"{n} EM reconstructions x {a.niter} iterations, nx in {{64..160}}, nz in {{32..96}}, "
                     f"60-128 views, PSF 11-37 (separable depth-dependent Gaussians)",
         "geometries": [[w["nx"], w["nz"], w["nview"], w["psf"]] for w in work],
@@ -114,7 +123,7 @@ def main(argv=None):
         "speedup_graph_tuned_vs_plain": t_plain / t_graph_tuned,
         "graph_bitwise_equal_to_plain": bool(same), "kernels_per_graph_launch": kernels,
         "setup_s": setup_s, "autotune_s": tune_s, "tunings": tunings,
-    }))
+    })
 
 
 if __name__ == "__main__":

@@ -12,9 +12,15 @@ request's image is copied back, its plan released and its slot reused at once.
 ``serve_plain`` runs the same requests one at a time through the same library
 calls (the baseline the server is compared with).
 
+Admission is by free device memory: the budget is the device's free memory
+when the server starts (``cudaMemGetInfo``, less a reserve), and before each
+admission the device's live free memory is checked again, less what admitted
+requests whose plans are still being built will take, so memory taken by
+anything else on the device holds requests back.
+
 The scheduler is host logic over an ``Executor``; ``GpuExecutor`` drives the
-library, ``FakeExecutor`` (tests) simulates a device-memory budget and a kernel
-clock without a GPU.
+library, ``FakeExecutor`` (tests) simulates device memory and a kernel clock
+without a GPU.
 """
 from __future__ import annotations
 
@@ -77,7 +83,21 @@ class GpuExecutor:
         self.iters_per_step = max(1, int(iters_per_step))
         self.pool = cf.ThreadPoolExecutor(max_workers=1)
         self.plan_bytes_seen = []
+        self._pending = {}          # id(handle) -> bytes promised to a plan still being built
         self.t0 = time.perf_counter()
+
+    def free_bytes(self) -> int:
+        """Device memory free right now: cudaMemGetInfo's free bytes plus what
+        torch's caching allocator holds unused (reusable by request tensors)."""
+        torch = self.torch
+        free, _total = torch.cuda.mem_get_info(self.device)
+        cached = torch.cuda.memory_reserved(self.device) - torch.cuda.memory_allocated(self.device)
+        return int(free + max(0, cached))
+
+    def pending_bytes(self) -> int:
+        """Memory promised to admitted requests whose plans are not built yet
+        (not visible in free_bytes() until they are)."""
+        return int(sum(self._pending.values()))
 
     def now(self) -> float:
         return time.perf_counter() - self.t0
@@ -111,8 +131,10 @@ class GpuExecutor:
 
     def start(self, req: Request, slot: int):
         st = self.streams[slot % len(self.streams)]
-        return {"future": self.pool.submit(self._create, req, st), "plan": None, "stream": st,
-                "left": req.niter, "event": None}
+        h = {"future": self.pool.submit(self._create, req, st), "plan": None, "stream": st,
+             "left": req.niter, "event": None}
+        self._pending[id(h)] = self.plan_bytes(req)
+        return h
 
     def step(self, h) -> None:
         """Enqueue the next EM iterations of a request on its stream (asynchronous)."""
@@ -125,12 +147,12 @@ class GpuExecutor:
         h["event"] = ev
         h["left"] -= n
 
-    @staticmethod
-    def ready(h) -> bool:
+    def ready(self, h) -> bool:
         if h["plan"] is None:
             if not h["future"].done():
                 return False
             h["plan"], h["x"], h["y"], h["rbar"] = h["future"].result()
+            self._pending.pop(id(h), None)
         return h["event"] is None or h["event"].query()
 
     def finish(self, h):
@@ -151,15 +173,30 @@ class GpuExecutor:
 class FakeExecutor:
     """Simulated device for scheduler tests: a memory figure per request and a
     clock; every admitted request's EM iteration takes ``iter_cost`` and
-    iterations of different requests overlap fully."""
+    iterations of different requests overlap fully.  ``device_bytes`` is the
+    simulated device memory (None: unlimited); ``other_use(t)`` is memory taken
+    at time t by something other than the server."""
 
-    def __init__(self, iter_cost: float = 0.01, plan_cost: float = 0.0):
+    def __init__(self, iter_cost: float = 0.01, plan_cost: float = 0.0, device_bytes=None, other_use=None):
         self.t = 0.0
         self.iter_cost, self.plan_cost = iter_cost, plan_cost
+        self.device_bytes = device_bytes
+        self.other_use = other_use
+        self.held = 0
         self.log = []
 
     def now(self) -> float:
         return self.t
+
+    def free_bytes(self):
+        if self.device_bytes is None:
+            return None
+        other = self.other_use(self.t) if self.other_use else 0
+        return self.device_bytes - self.held - other
+
+    @staticmethod
+    def pending_bytes() -> int:
+        return 0
 
     @staticmethod
     def plan_bytes(req: Request) -> int:
@@ -167,8 +204,9 @@ class FakeExecutor:
 
     def start(self, req, slot):
         self.t += self.plan_cost
+        self.held += self.plan_bytes(req)
         self.log.append(("start", req.rid, self.t))
-        return {"rid": req.rid, "left": req.niter, "busy_until": self.t}
+        return {"rid": req.rid, "left": req.niter, "busy_until": self.t, "bytes": self.plan_bytes(req)}
 
     def step(self, h):
         h["busy_until"] = max(h["busy_until"], self.t) + self.iter_cost
@@ -186,6 +224,7 @@ class FakeExecutor:
             self.t = min(cands)
 
     def finish(self, h):
+        self.held -= h["bytes"]
         self.log.append(("finish", h["rid"], self.t))
         return None
 
@@ -197,24 +236,43 @@ class ServeStats:
     makespan: float = 0.0
     peak_bytes: int = 0
     peak_active: int = 0
+    held_back: int = 0          # admissions deferred because the device's live free memory was short
+    budget: int = 0
 
     def summary(self) -> dict:
         lat = np.array([r.latency for r in self.results]) if self.results else np.zeros(1)
         return {"requests": len(self.results), "recon_per_s": len(self.results) / max(self.makespan, 1e-9),
                 "p50_s": float(np.percentile(lat, 50)), "p95_s": float(np.percentile(lat, 95)),
                 "p99_s": float(np.percentile(lat, 99)), "makespan_s": self.makespan,
-                "peak_active": self.peak_active, "peak_bytes": self.peak_bytes}
+                "peak_active": self.peak_active, "peak_bytes": self.peak_bytes, "budget_bytes": self.budget,
+                "held_back_by_free_memory": self.held_back}
 
 
-def serve(requests, executor, mem_budget: int, max_active: int = 16, poll_sleep: float = 0.0) -> ServeStats:
+RESERVE_BYTES = 2 << 30  # device memory the server leaves free for everything else
+
+
+def serve(requests, executor, mem_budget=None, max_active: int = 16, poll_sleep: float = 0.0,
+          reserve_bytes: int = RESERVE_BYTES) -> ServeStats:
     """Continuous batching: admit by memory and slots, interleave EM iterations
-    round-robin, retire finished requests immediately."""
+    round-robin, retire finished requests immediately.
+
+    mem_budget: bytes the server may hold at once; None takes the device's free
+    memory at the start less ``reserve_bytes``.  Each admission also needs the
+    request's bytes free on the device at that moment (live free memory, less
+    the bytes of plans still being built, less the reserve), unless nothing is
+    admitted (memory released in stream order may not show as free yet)."""
+    free0 = executor.free_bytes() if hasattr(executor, "free_bytes") else None
+    if mem_budget is None:
+        if free0 is None:
+            raise ValueError("mem_budget is required when the executor cannot report free device memory")
+        mem_budget = free0 - reserve_bytes
     pending = sorted(requests, key=lambda r: r.arrival)
     queue: list = []            # arrived, not admitted (FIFO)
     active: list = []           # (request, handle, admitted_at, slot)
     used = 0
     slots_free = list(range(max_active))
     stats = ServeStats()
+    stats.budget = int(mem_budget)
     pi = 0
     while pi < len(pending) or queue or active:
         now = executor.now()
@@ -228,6 +286,11 @@ def serve(requests, executor, mem_budget: int, max_active: int = 16, poll_sleep:
                 raise ValueError(f"request {queue[0].rid} needs {need} bytes, more than the whole budget")
             if used + need > mem_budget:
                 break
+            if active and free0 is not None:
+                live = executor.free_bytes() - executor.pending_bytes() - reserve_bytes
+                if need > live:
+                    stats.held_back += 1
+                    break
             req = queue.pop(0)
             slot = slots_free.pop(0)
             h = executor.start(req, slot)
@@ -296,28 +359,77 @@ def serve_plain(requests, executor) -> ServeStats:
 # --------------------------------------------------------------------------- workload
 def make_requests(n: int, rate: float, seed: int = 0, large_frac: float = 0.2, iters=(16, 32),
                   sizes=(64, 96, 128, 160), nzs=(32, 48, 64, 80, 96), views=(60, 90, 120, 128),
-                  psfs=(11, 21, 29, 37), large=(192, 128, 128, 37)):
-    """Poisson arrivals of reconstructions of mixed sizes (synthetic phantoms)."""
+                  psfs=(11, 21, 29, 37), large=(192, 128, 128, 37), device=None, counts: float = 1e7,
+                  background: float = 0.1):
+    """Poisson arrivals of reconstructions of mixed sizes (synthetic phantoms).
+
+    With ``device`` set, each request's measurements are simulated with the
+    library's own projector: y ~ Poisson(A x_true + rbar), A x_true scaled to
+    ``counts`` expected primary counts and rbar a uniform background carrying
+    ``background`` of them (the paper's 10 % uniform scatter).  Without a
+    device (scheduler tests on CPU) the counts are drawn around a constant mean.
+    The large cases use the anisotropic depth-dependent PSF of the paper-scale
+    workload, the others isotropic Gaussians with FWHM 1 -> 4 pixels.
+    """
     from . import synthetic
     rng = np.random.default_rng(seed)
     t = 0.0
     reqs = []
     for rid in range(n):
         t += rng.exponential(1.0 / rate)
-        if rng.uniform() < large_frac:
+        big = rng.uniform() < large_frac
+        if big:
             nx, nz, nv, p = large
         else:
             nx, nz, nv, p = (int(rng.choice(sizes)), int(rng.choice(nzs)), int(rng.choice(views)),
                              int(rng.choice(psfs)))
         x, mu, body = synthetic.small_phantom(nx, nz, seed * 100003 + rid)
-        fx, fz = synthetic.depth_psf_factors(nx, p, p, 1.0, 4.0, aniso=False)
-        # counts: a smooth positive sinogram-like mean (the projector is not run here)
-        mean = np.full((nv, nz, nx), float(x.sum()) / (nz * nx) * 0.5 + 1.0, np.float32)
-        y = rng.poisson(mean).astype(np.float32)
-        rbar = np.full_like(y, 0.1 * float(mean.mean()))
-        reqs.append(Request(rid, t, nx, nz, nv, int(rng.integers(iters[0], iters[1] + 1)), mu, fx, fz, y, rbar,
+        if big:
+            fx, fz = synthetic.depth_psf_factors(nx, p, p, 1.5, 9.0, aniso=True)
+        else:
+            fx, fz = synthetic.depth_psf_factors(nx, p, p, 1.0, 4.0, aniso=False)
+        niter = int(rng.integers(iters[0], iters[1] + 1))
+        if device is None:
+            mean = np.full((nv, nz, nx), float(x.sum()) / (nz * nx) * 0.5 + 1.0, np.float32)
+            y = rng.poisson(mean).astype(np.float32)
+            rbar = np.full_like(y, 0.1 * float(mean.mean()))
+        else:
+            y, rbar = _simulate_counts(x, mu, fx, fz, nv, device, counts, background,
+                                       np.random.default_rng([seed, rid]))
+        reqs.append(Request(rid, t, nx, nz, nv, niter, mu, fx, fz, y, rbar,
                             np.where(body, 1.0, 0.0).astype(np.float32) + 0.01))
     return reqs
+
+
+def _simulate_counts(x, mu, fx, fz, nview, device, counts, background, rng):
+    """y ~ Poisson(A x + rbar) with A the library's projector for this geometry."""
+    import torch
+
+    from .projector import SpectPlan
+    nz, nx, _ = x.shape
+    plan = SpectPlan(nx, nz, nview, mu=mu, dy=1.0, fx=fx, fz=fz, device=device)
+    primary = plan.forward(torch.from_numpy(np.ascontiguousarray(x, np.float32)).to(device))
+    plan.check()
+    plan.close()
+    primary = primary.double().cpu().numpy()
+    primary *= counts / max(primary.sum(), 1e-30)
+    rbar = np.full(primary.shape, background * primary.sum() / primary.size)
+    y = rng.poisson(primary + rbar).astype(np.float32)
+    return y, rbar.astype(np.float32)
+
+
+def compare(requests, streams: int = 4, max_active: int = 8, iters_per_step: int = 2, device="cuda") -> dict:
+    """Serve the requests with continuous batching, then one at a time through
+    the same library calls; latency percentiles and throughput of both, and
+    whether every request's image is bitwise the same in both runs."""
+    ex = GpuExecutor(device=device, n_streams=streams, keep_images=True, iters_per_step=iters_per_step)
+    st_served = serve(requests, ex, None, max_active)
+    ex.close()
+    ex2 = GpuExecutor(device=device, n_streams=1, keep_images=True, iters_per_step=iters_per_step)
+    st_plain = serve_plain(requests, ex2)
+    ex2.close()
+    same = all(a.x is not None and np.array_equal(a.x, b.x) for a, b in zip(st_served.results, st_plain.results))
+    return {"served": st_served.summary(), "plain": st_plain.summary(), "identical_images": bool(same)}
 
 
 def main(argv=None):
@@ -326,17 +438,10 @@ def main(argv=None):
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--streams", type=int, default=4)
     ap.add_argument("--max-active", type=int, default=8)
-    ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--large-frac", type=float, default=0.2)
     a = ap.parse_args(argv)
-    reqs = make_requests(a.requests, a.rate, large_frac=a.large_frac)
-    ex = GpuExecutor(n_streams=a.streams, keep_images=False)
-    served = serve(reqs, ex, int(a.budget_gb * 2**30), a.max_active).summary()
-    ex.close()
-    ex2 = GpuExecutor(n_streams=1, keep_images=False)
-    plain = serve_plain(reqs, ex2).summary()
-    ex2.close()
-    print(json.dumps({"served": served, "plain": plain}))
+    reqs = make_requests(a.requests, a.rate, large_frac=a.large_frac, device="cuda")
+    print(json.dumps(compare(reqs, a.streams, a.max_active)))
 
 
 if __name__ == "__main__":

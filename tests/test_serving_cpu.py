@@ -53,3 +53,34 @@ def test_concurrency_beats_one_at_a_time_on_the_simulated_device():
     served = serve(reqs, FakeExecutor(iter_cost=0.01), mem_budget=1 << 40, max_active=8).summary()
     plain = serve_plain(reqs, FakeExecutor(iter_cost=0.01)).summary()
     assert served["p99_s"] < plain["p99_s"] and served["recon_per_s"] > plain["recon_per_s"]
+
+
+def test_budget_defaults_to_free_device_memory_less_the_reserve():
+    reqs = [_req(i, 0.0) for i in range(8)]
+    per = FakeExecutor.plan_bytes(reqs[0])
+    ex = FakeExecutor(iter_cost=0.01, device_bytes=4 * per + 1000)
+    st = serve(reqs, ex, mem_budget=None, max_active=8, reserve_bytes=1000)
+    assert st.budget == 4 * per and st.peak_active == 4 and st.peak_bytes <= 4 * per
+    assert len(st.results) == 8
+
+
+def test_memory_taken_by_another_tenant_holds_admission_back():
+    """The budget fits 4 requests, but from t = 0.005 s something else holds
+    half the device: admissions after that wait until the live free memory
+    allows them, and every request still completes."""
+    reqs = [_req(i, 0.001 * i) for i in range(8)]
+    per = FakeExecutor.plan_bytes(reqs[0])
+    total = 4 * per
+    ex = FakeExecutor(iter_cost=0.01, device_bytes=total, other_use=lambda t: 2 * per if t >= 0.005 else 0)
+    st = serve(reqs, ex, mem_budget=None, max_active=8, reserve_bytes=0)
+    assert len(st.results) == 8
+    assert st.held_back > 0
+    # while the other tenant holds 2 requests' worth, at most 2 requests are resident
+    for t in np.arange(0.006, st.makespan, 0.0005):
+        resident = sum(1 for r in st.results if r.admitted <= t < r.done and r.admitted >= 0.005)
+        assert resident <= 2
+
+
+def test_serving_without_a_budget_needs_a_device_that_reports_free_memory():
+    with pytest.raises(ValueError, match="mem_budget"):
+        serve([_req(0, 0.0)], FakeExecutor(), mem_budget=None)
