@@ -688,9 +688,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
     }
     __syncthreads();
 
-    // the thread's first work item of each pass (the same for every plane)
+    // the thread's first work item of each pass and the step to its next one
+    // (the same for every plane: the divisions stay out of the plane loop)
     const int ip_ib = tid / nz, ip_k = tid - ip_ib * nz;    // i-pass: (column run, k)
     const int kp_kb = tid / ti, kp_i = tid - kp_kb * ti;    // k-pass: (k run, column)
+    const int ip_dib = T / nz, ip_dk = T - ip_dib * nz;
+    const int kp_dkb = T / ti, kp_di = T - kp_dkb * ti;
     unsigned phases = 0u;                                   // bit b: parity of buffer b's barrier
     for (int j = j_begin; j < j_end; ++j) {
         const int b = (j - j_begin) & 1;
@@ -719,8 +722,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
                     for (int c = 0; c < CX; ++c)
                         if (li + c < ti) ur[c * d.kpu] = o[c];
                 }
-                ib += T / nz;  // next item: it + T
-                k += T % nz;
+                ib += ip_dib;  // next item: it + T
+                k += ip_dk;
                 if (k >= nz) k -= nz, ++ib;
             }
         }
@@ -786,8 +789,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fwd_sep_fused(Geometry g, 
                 a.w += o[4 * c4 + 3];
                 acc4[c4] = a;
             }
-            kb += T / ti;  // next item: it + T
-            i += T % ti;
+            kb += kp_dkb;  // next item: it + T
+            i += kp_di;
             if (i >= ti) i -= ti, ++kb;
         }
         __syncthreads();
@@ -893,6 +896,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
     }
     __syncthreads();
 
+    // the thread's first work item of each pass and the step to its next one
+    // (the same for every plane: the divisions stay out of the plane loop)
+    const int ka_kb = tid / nvr, ka_r = tid - ka_kb * nvr;  // k-adjoint: (k run, detector row)
+    const int ka_dkb = T / nvr, ka_dr = T - ka_dkb * nvr;
+    const int ia_ib = tid / nz, ia_k = tid - ia_ib * nz;    // i-adjoint: (column run, k)
+    const int ia_dib = T / nz, ia_dk = T - ia_dib * nz;
     unsigned phases = 0u;  // bit b: parity of buffer b's barrier
     for (int j = j_begin; j < j_end; ++j) {
         const int n = j - j_begin, b = n & 1;
@@ -901,8 +910,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
         // k-adjoint: Zb[k][C+i] = sum_b' fz~(b') v(i, k+b'-cz), lanes over i.
         // The first and last detector rows, where replicate padding folds
         // taps together, take their edge-class taps instead of the interior ones.
-        for (int it = tid; it < nvr * d.nkb; it += T) {
-            const int kb = it / nvr, r = it - kb * nvr;  // detector row vlo + r
+        int kb = ka_kb, r = ka_r;  // detector row vlo + r
+        for (int it = tid; it < nvr * d.nkb; it += T, kb += ka_dkb, r += ka_dr) {
+            if (r >= nvr) r -= nvr, ++kb;
             const float* vr = V + r * d.kpu;
             float win[WZ];
             load_window_f4<P>(vr + kb * CZ, win);
@@ -942,8 +952,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adj_sep_fused(Geometry g, 
         const bool ok = mbar_wait_bounded(bar + b, (phases >> b) & 1u);
         phases ^= 1u << b;
         if (ok) {
-            for (int it = tid; it < nz * nibt; it += T) {
-                const int ib = it / nz, k = it - ib * nz;
+            int ib = ia_ib, k = ia_k;
+            for (int it = tid; it < nz * nibt; it += T, ib += ia_dib, k += ia_dk) {
+                if (k >= nz) k -= nz, ++ib;
                 const int li = ib * CX;  // first column of this run, relative to the tile
                 const float* zr = Zb + k * d.wz + li;
                 float win[4 * ((CX + P - 1 + 3) / 4)];
