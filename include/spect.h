@@ -182,6 +182,41 @@ spect_status spect_em_step_reg(spect_plan plan, float* x, const float* y, const 
                                float beta, int niter, spect_stream stream);
 
 /*
+ * The element-wise steps of one EM iteration, Eqs. (7)-(8), as separate calls
+ * with their gradients, for training through an unrolled reconstruction
+ * (Algorithm 3, Section II-B): with spect_forward (A) and spect_back (A') they
+ * make up the update x+ = F(x, A'(y / (A x + rbar)), u) that spect_em_step_reg
+ * runs fused, in a form an automatic-differentiation system can chain.  All
+ * pointers are device, n elements each (rbar and u may be NULL as stated), FP32;
+ * work is queued on `stream`.  Element-wise, so any layout works as long as the
+ * arrays of one call share it.  Errors: SPECT_EINVAL (NULL pointers, beta < 0 or
+ * not finite, u missing with beta > 0), SPECT_ECUDA.
+ *
+ * spect_em_ratio: ratio = y / (ybar + rbar), 0 where ybar + rbar <= 0 (the
+ *   guard of spect_em_step); ybar is A x.
+ * spect_em_ratio_backward: g_ybar = dL/dybar from g_ratio = dL/dratio:
+ *   g_ybar = -g_ratio * ratio / (ybar + rbar), 0 where the guard applies.
+ * spect_em_update: out = the update of spect_em_step_reg from x, e = A'(ratio),
+ *   s = A'1 and u (beta = 0: x e / s, u unused); the same arithmetic as the
+ *   fused step.
+ * spect_em_update_backward: from g_out = dL/dout, g_x = g_out e / q,
+ *   g_e = g_out x / q and g_u = g_out beta out / q, q = sqrt(d^2 + 4 beta x e),
+ *   d = s - beta u (q = s at beta = 0): the implicit derivative of
+ *   beta out^2 + d out - x e = 0; all three are 0 where the forward guard set
+ *   out to 0.  Any of g_x, g_e, g_u may be NULL (not computed); g_u is filled
+ *   with 0 when beta = 0.
+ */
+spect_status spect_em_ratio(size_t n, const float* ybar, const float* y, const float* rbar, float* ratio,
+                            spect_stream stream);
+spect_status spect_em_ratio_backward(size_t n, const float* ybar, const float* y, const float* rbar,
+                                     const float* g_ratio, float* g_ybar, spect_stream stream);
+spect_status spect_em_update(size_t n, const float* x, const float* e, const float* s, const float* u, float beta,
+                             float* out, spect_stream stream);
+spect_status spect_em_update_backward(size_t n, const float* x, const float* e, const float* s, const float* u,
+                                      float beta, const float* g_out, float* g_x, float* g_e, float* g_u,
+                                      spect_stream stream);
+
+/*
  * spect_sensitivity -- copy the plan's sensitivity s = A'1 (the d(0) term
  * of Eq. (8)) into s (device, nx*ny*nz).  Computes and caches it first if
  * needed.  Errors as spect_forward.

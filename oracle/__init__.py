@@ -250,6 +250,77 @@ def em_step(x, y, rbar, mu, psf, dy: float, angles, s=None, nthreads: int = 0,
     return out
 
 
+def em_ratio(ybar, y, rbar=None) -> np.ndarray:
+    """The ratio y / (ybar + rbar) of Eq. (8), 0 where ybar + rbar <= 0 (the guard of em_step)."""
+    yb = _f64(ybar) + (0.0 if rbar is None else _f64(rbar))
+    out = np.zeros_like(yb)
+    pos = yb > 0
+    out[pos] = _f64(y)[pos] / yb[pos]
+    return out
+
+
+def em_ratio_vjp(ybar, y, rbar, g) -> np.ndarray:
+    """dL/dybar of em_ratio given dL/dratio: d(y/(ybar + rbar))/dybar = -y/(ybar + rbar)^2."""
+    yb = _f64(ybar) + (0.0 if rbar is None else _f64(rbar))
+    out = np.zeros_like(yb)
+    pos = yb > 0
+    out[pos] = -_f64(g)[pos] * _f64(y)[pos] / yb[pos] ** 2
+    return out
+
+
+def em_root(x, e, s, u, beta: float) -> np.ndarray:
+    """The update of Eqs. (7)-(8) from x_k, e = A'(y / (A x_k + rbar)), s = A'1 and u:
+    the non-negative root of beta x^2 + d x - x_k e = 0, d = s - beta u.  beta = 0: the
+    MLEM update x e / s (0 where s <= 0).  beta > 0: where d >= 0 the root is
+    written 2 x e / (d + sqrt(d^2 + 4 beta x e)) (no cancellation for small beta),
+    where d < 0 as (sqrt(d^2 + 4 beta x e) - d) / (2 beta); 0 where the denominator
+    is not positive."""
+    x = _f64(x)
+    e = _f64(e)
+    s = _f64(s)
+    xe = x * e
+    out = np.zeros_like(x)
+    if beta == 0:
+        ok = s > 0
+        out[ok] = xe[ok] / s[ok]
+        return out
+    d = s - beta * _f64(u)
+    root = np.sqrt(d * d + 4.0 * beta * xe)
+    pos = d >= 0
+    den = d + root
+    ok = pos & (den > 0)
+    out[ok] = 2.0 * xe[ok] / den[ok]
+    neg = ~pos
+    out[neg] = (root[neg] - d[neg]) / (2.0 * beta)
+    return out
+
+
+def em_root_vjp(x, e, s, u, beta: float, g):
+    """(dL/dx, dL/de, dL/du) of em_root given dL/dx+.  Differentiating
+    beta x+^2 + d x+ - x e = 0 (d = s - beta u) implicitly:
+    (2 beta x+ + d) dx+ = e dx + x de + beta x+ du, with 2 beta x+ + d =
+    sqrt(d^2 + 4 beta x e) = q; at beta = 0, x+ = x e / s and q = s.  Zero where
+    em_root's guard set x+ to 0."""
+    x = _f64(x)
+    e = _f64(e)
+    s = _f64(s)
+    g = _f64(g)
+    gx, ge, gu = np.zeros_like(x), np.zeros_like(x), np.zeros_like(x)
+    if beta == 0:
+        ok = s > 0
+        gx[ok] = g[ok] * e[ok] / s[ok]
+        ge[ok] = g[ok] * x[ok] / s[ok]
+        return gx, ge, gu
+    d = s - beta * _f64(u)
+    q = np.sqrt(d * d + 4.0 * beta * x * e)
+    ok = ((d < 0) | (d + q > 0)) & (q > 0)
+    xp = em_root(x, e, s, u, beta)
+    gx[ok] = g[ok] * e[ok] / q[ok]
+    ge[ok] = g[ok] * x[ok] / q[ok]
+    gu[ok] = g[ok] * beta * xp[ok] / q[ok]
+    return gx, ge, gu
+
+
 def em_step_reg(x, y, rbar, u, beta: float, mu, psf, dy: float, angles, s=None, nthreads: int = 0) -> np.ndarray:
     """One inner iteration of the regularised EM update, Eqs. (7)-(8):
 
@@ -276,18 +347,7 @@ def em_step_reg(x, y, rbar, u, beta: float, mu, psf, dy: float, angles, s=None, 
     pos = ybar > 0
     ratio[pos] = y[pos] / ybar[pos]
     e = back(ratio, mu, psf, dy, angles, nthreads)
-    d = s - beta * u
-    xe = x * e
-    root = np.sqrt(d * d + 4.0 * beta * xe)
-    out = np.zeros_like(x)
-    pos = d >= 0
-    den = d + root
-    ok = pos & (den > 0)
-    out[ok] = 2.0 * xe[ok] / den[ok]
-    neg = ~pos
-    if beta > 0:
-        out[neg] = (root[neg] - d[neg]) / (2.0 * beta)
-    return out
+    return em_root(x, e, s, u, beta)
 
 
 def poisson_loglik(x, y, rbar, mu, psf, dy: float, angles, nthreads: int = 0) -> float:

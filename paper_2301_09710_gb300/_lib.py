@@ -68,6 +68,16 @@ def load(path: str = LIB_PATH):
         lib.spect_em_step.restype = st
         lib.spect_em_step_reg.argtypes = [vp, vp, vp, vp, vp, ctypes.c_float, i, vp]
         lib.spect_em_step_reg.restype = st
+        sz = ctypes.c_size_t
+        f32 = ctypes.c_float
+        lib.spect_em_ratio.argtypes = [sz, vp, vp, vp, vp, vp]
+        lib.spect_em_ratio.restype = st
+        lib.spect_em_ratio_backward.argtypes = [sz, vp, vp, vp, vp, vp, vp]
+        lib.spect_em_ratio_backward.restype = st
+        lib.spect_em_update.argtypes = [sz, vp, vp, vp, vp, f32, vp, vp]
+        lib.spect_em_update.restype = st
+        lib.spect_em_update_backward.argtypes = [sz, vp, vp, vp, vp, f32, vp, vp, vp, vp, vp]
+        lib.spect_em_update_backward.restype = st
         lib.spect_sensitivity.argtypes = [vp, vp, vp]
         lib.spect_sensitivity.restype = st
         lib.spect_plan_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),

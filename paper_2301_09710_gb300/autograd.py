@@ -4,8 +4,11 @@ and the unrolled CNN-regularised EM of Algorithm 3 (Section II-B).
 * ``project(x, plan)`` is A x with backward A' g; ``backproject(v, plan)`` is A' v
   with backward A g.  Both run the library's kernels (the transpose is exact, so
   these are the true Jacobians) and never store rotated intermediates.
-* ``em_update`` is one inner iteration of Eqs. (7)-(8) written with them, so
-  gradients flow through A, A' and the closed-form update.
+* ``em_update`` is one inner iteration of Eqs. (7)-(8) written with them and
+  with the library's element-wise EM kernels (the ratio y / (A x + rbar) and the
+  closed-form update, each with a hand-written gradient kernel: the implicit
+  derivative of beta x+^2 + d x+ - x e = 0), so gradients flow through A, A' and
+  the update with every step in the library's kernels.
 * ``UnrolledEM`` unrolls K outer iterations u = g_theta(x_k), x_{k+1} = EM(x_k, u)
   with a small 3D CNN g_theta and per-iteration activation checkpointing
   (``torch.utils.checkpoint``): only the iterates are kept, everything inside an
@@ -19,6 +22,7 @@ import torch
 import torch.nn as nn
 import torch.utils.checkpoint as ckpt
 
+from . import projector as _pj
 from .projector import SpectPlan
 
 
@@ -54,31 +58,62 @@ def backproject(v: torch.Tensor, plan) -> torch.Tensor:
     return _BackProject.apply(v, plan)
 
 
+class _Ratio(torch.autograd.Function):
+    """y / (ybar + rbar) (0 where ybar + rbar <= 0); differentiable in ybar."""
+
+    @staticmethod
+    def forward(ctx, ybar, y, rbar):
+        ybar, y = ybar.contiguous(), y.contiguous()
+        rbar = rbar.contiguous() if rbar is not None else None
+        ctx.save_for_backward(ybar, y, rbar)
+        return _pj.em_ratio(ybar, y, rbar)
+
+    @staticmethod
+    def backward(ctx, g):
+        ybar, y, rbar = ctx.saved_tensors
+        return _pj.em_ratio_backward(ybar, y, rbar, g.contiguous()), None, None
+
+
+class _Update(torch.autograd.Function):
+    """The closed-form update of Eqs. (7)-(8); differentiable in x, e and u."""
+
+    @staticmethod
+    def forward(ctx, x, e, s, u, beta):
+        x, e, s = x.contiguous(), e.contiguous(), s.contiguous()
+        u = u.contiguous() if (u is not None and beta > 0) else None
+        ctx.beta = float(beta)
+        ctx.save_for_backward(x, e, s, u)
+        return _pj.em_update(x, e, s, u, float(beta))
+
+    @staticmethod
+    def backward(ctx, g):
+        x, e, s, u = ctx.saved_tensors
+        gx, ge, gu = _pj.em_update_backward(x, e, s, u, ctx.beta, g.contiguous())
+        return gx, ge, None, gu, None
+
+
+def em_ratio(ybar, y, rbar):
+    return _Ratio.apply(ybar, y, rbar)
+
+
+def em_root(x, e, s, u, beta):
+    return _Update.apply(x, e, s, u, beta)
+
+
 def em_update(x, y, rbar, plan, s, u=None, beta: float = 0.0):
     """One inner EM iteration, Eqs. (7)-(8), differentiable in x and u.
 
     beta == 0: x e / s (MLEM).  beta > 0: the non-negative root of
     beta x'^2 + d x' - x e = 0, d = s - beta u, in the cancellation-free form
-    for the sign of d.  Guards as the library: ratio 0 where A x + rbar <= 0.
+    for the sign of d.  Guards as the library: ratio 0 where A x + rbar <= 0,
+    voxel 0 where the root is not finite and positive.  Every step runs in the
+    library's kernels: A, the ratio, A', the update (and their gradients).
     """
-    ybar = project(x, plan)
-    if rbar is not None:
-        ybar = ybar + rbar
-    pos = ybar > 0
-    ratio = torch.where(pos, y / torch.where(pos, ybar, torch.ones_like(ybar)), torch.zeros_like(ybar))
+    ratio = em_ratio(project(x, plan), y, rbar)
     e = backproject(ratio, plan)
-    xe = x * e
     if beta == 0.0 or u is None:
-        ok = s > 0
-        return torch.where(ok, xe / torch.where(ok, s, torch.ones_like(s)), torch.zeros_like(x))
-    d = s - beta * u
-    root = torch.sqrt(d * d + 4.0 * beta * xe)
-    dpos = d >= 0
-    den = d + root
-    safe = dpos & (den > 0)
-    a = 2.0 * xe / torch.where(safe, den, torch.ones_like(den))
-    b = (root - d) / (2.0 * beta)
-    return torch.where(safe, a, torch.where(dpos, torch.zeros_like(a), b))
+        return em_root(x, e, s, None, 0.0)
+    return em_root(x, e, s, u, beta)
 
 
 class Regularizer3D(nn.Module):

@@ -211,7 +211,7 @@ __device__ __forceinline__ float em_update(float x, float e, float s, float u, f
 {
     const float xe = x * e;
     if (beta == 0.f) return s > 0.f ? xe / s : 0.f;
-    const float d = s - beta * u;
+    const float d = fmaf(-beta, u, s);  // explicit: every kernel rounds d the same way
     const float root = sqrtf(fmaf(d, d, 4.f * beta * xe));
     if (d >= 0.f) {
         const float den = d + root;

@@ -45,6 +45,55 @@ def fp32_peak(stream=None) -> dict:
     return {"ffma_tflops": a.value, "ffma2_tflops": b.value}
 
 
+def _ew_check(*ts):
+    ref = next(t for t in ts if t is not None)
+    for t in ts:
+        if t is not None and (t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous()
+                              or t.numel() != ref.numel() or t.device != ref.device):
+            raise ValueError("element-wise EM arrays must be contiguous float32 CUDA tensors of one size and device")
+    return ref.numel()
+
+
+def em_ratio(ybar, y, rbar=None, out=None, stream=None):
+    """ratio = y / (ybar + rbar), 0 where ybar + rbar <= 0 (spect_em_ratio)."""
+    n = _ew_check(ybar, y, rbar)
+    out = torch.empty_like(ybar) if out is None else out
+    _ew_check(ybar, out)
+    _lib.check(_lib.load().spect_em_ratio(n, _ptr(ybar), _ptr(y), _ptr(rbar), _ptr(out), _stream_handle(stream)))
+    return out
+
+
+def em_ratio_backward(ybar, y, rbar, g_ratio, stream=None):
+    """dL/dybar of em_ratio from dL/dratio (spect_em_ratio_backward)."""
+    n = _ew_check(ybar, y, rbar, g_ratio)
+    out = torch.empty_like(ybar)
+    _lib.check(_lib.load().spect_em_ratio_backward(n, _ptr(ybar), _ptr(y), _ptr(rbar), _ptr(g_ratio), _ptr(out),
+                                                   _stream_handle(stream)))
+    return out
+
+
+def em_update(x, e, s, u=None, beta: float = 0.0, out=None, stream=None):
+    """The EM update of Eqs. (7)-(8) from x, e = A'(ratio), s = A'1, u (spect_em_update)."""
+    n = _ew_check(x, e, s, u if beta > 0 else None)
+    out = torch.empty_like(x) if out is None else out
+    _ew_check(x, out)
+    _lib.check(_lib.load().spect_em_update(n, _ptr(x), _ptr(e), _ptr(s), _ptr(u if beta > 0 else None),
+                                           ctypes.c_float(beta), _ptr(out), _stream_handle(stream)))
+    return out
+
+
+def em_update_backward(x, e, s, u, beta: float, g_out, stream=None):
+    """(dL/dx, dL/de, dL/du) of em_update from dL/dout (spect_em_update_backward);
+    dL/du is None when beta == 0."""
+    n = _ew_check(x, e, s, g_out, u if beta > 0 else None)
+    gx, ge = torch.empty_like(x), torch.empty_like(x)
+    gu = torch.empty_like(x) if beta > 0 else None
+    _lib.check(_lib.load().spect_em_update_backward(n, _ptr(x), _ptr(e), _ptr(s), _ptr(u if beta > 0 else None),
+                                                    ctypes.c_float(beta), _ptr(g_out), _ptr(gx), _ptr(ge), _ptr(gu),
+                                                    _stream_handle(stream)))
+    return gx, ge, gu
+
+
 def forward_static(x, nview: int, fx, fz, mu=None, dy: float = 1.0, angles=None, out=None, stream=None):
     """v = A x through spect_forward_static: no plan, no device allocation in
     the library (for callers that cannot allocate; see include/spect.h).

@@ -1,5 +1,8 @@
 """The differentiable EM update and the unrolled network, checked on CPU in FP64
-with the oracle standing in for A / A' (torch.autograd.gradcheck)."""
+with the oracle standing in for A / A' and for the element-wise EM steps (the
+ratio and the closed-form update with their hand-derived gradients), through
+torch.autograd.gradcheck.  The library's own element-wise kernels are compared
+with the same oracle functions on the GPU (tests/test_gpu_autograd.py)."""
 import numpy as np
 import pytest
 
@@ -32,12 +35,51 @@ class _OB(torch.autograd.Function):
         return torch.from_numpy(oracle.forward(g.detach().numpy(), *ctx.args, nthreads=1)), None
 
 
+class _ORatio(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, ybar, y, rbar):
+        ctx.save_for_backward(ybar, y, rbar)
+        r = None if rbar is None else rbar.detach().numpy()
+        return torch.from_numpy(oracle.em_ratio(ybar.detach().numpy(), y.detach().numpy(), r))
+
+    @staticmethod
+    def backward(ctx, g):
+        ybar, y, rbar = ctx.saved_tensors
+        r = None if rbar is None else rbar.numpy()
+        return torch.from_numpy(oracle.em_ratio_vjp(ybar.numpy(), y.numpy(), r, g.numpy())), None, None
+
+
+class _ORoot(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, e, s, u, beta):
+        ctx.beta = beta
+        ctx.save_for_backward(x, e, s, u)
+        un = None if u is None else u.detach().numpy()
+        return torch.from_numpy(oracle.em_root(x.detach().numpy(), e.detach().numpy(), s.detach().numpy(), un,
+                                               beta))
+
+    @staticmethod
+    def backward(ctx, g):
+        x, e, s, u = ctx.saved_tensors
+        un = None if u is None else u.numpy()
+        gx, ge, gu = oracle.em_root_vjp(x.numpy(), e.numpy(), s.numpy(), un, ctx.beta, g.numpy())
+        return (torch.from_numpy(gx), torch.from_numpy(ge), None,
+                None if u is None else torch.from_numpy(gu), None)
+
+
+def use_oracle_em(monkeypatch):
+    """The element-wise EM steps of autograd.em_update on the FP64 oracle."""
+    monkeypatch.setattr(ag, "em_ratio", lambda ybar, y, rbar: _ORatio.apply(ybar, y, rbar))
+    monkeypatch.setattr(ag, "em_root", lambda x, e, s, u, beta: _ORoot.apply(x, e, s, u, beta))
+
+
 @pytest.fixture
 def tiny(monkeypatch):
     prob = synthetic.random_problem(21, nx=6, nz=3, nview=4, px=3, pz=3, mu_scale=0.1)
     args = (prob.mu.astype(np.float64), prob.psf.astype(np.float64), 1.0, oracle.default_angles(4))
     monkeypatch.setattr(ag, "project", lambda x, plan: _OA.apply(x, args))
     monkeypatch.setattr(ag, "backproject", lambda v, plan: _OB.apply(v, args))
+    use_oracle_em(monkeypatch)
     rng = np.random.default_rng(21)
     y = torch.from_numpy(rng.poisson(4.0, (4, 3, 6)).astype(np.float64))
     s = torch.from_numpy(oracle.sensitivity(*args))

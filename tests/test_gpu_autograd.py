@@ -146,6 +146,7 @@ class _OracleBack(torch.autograd.Function):
 
 def test_unrolled_em_gradient_matches_fp64_oracle_network(monkeypatch):
     import paper_2301_09710_gb300.autograd as ag
+    from test_autograd_cpu import use_oracle_em
     prob, ang = _small()
     plan = make_plan(prob, ang, "fused")
     psf = oracle_psf(prob, "fused")
@@ -160,6 +161,7 @@ def test_unrolled_em_gradient_matches_fp64_oracle_network(monkeypatch):
     args = (prob.mu, psf, prob.dy, ang)
     monkeypatch.setattr(ag, "project", lambda x, plan: _OracleProject.apply(x, args))
     monkeypatch.setattr(ag, "backproject", lambda v, plan: _OracleBack.apply(v, args))
+    use_oracle_em(monkeypatch)
     net64 = _unrolled(None, dtype=torch.float64, device="cpu")
     net64.cnn.load_state_dict({k: v.double().cpu() for k, v in net.cnn.state_dict().items()})
     net64._s = torch.from_numpy(oracle.sensitivity(prob.mu, psf, prob.dy, ang))
@@ -170,3 +172,71 @@ def test_unrolled_em_gradient_matches_fp64_oracle_network(monkeypatch):
     assert abs(loss.item() - loss64.item()) <= 1e-5 * abs(loss64.item())
     for a, b in zip(g_gpu, g_cpu):
         assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b) + 1e-9
+
+
+# ---------------------------------------------------------------- element-wise EM kernels and their gradients
+@pytest.mark.parametrize("beta", [0.0, 0.05, 0.7, 30.0])
+def test_em_update_kernels_match_oracle(beta):
+    """spect_em_update / spect_em_update_backward against the oracle's closed-form
+    root and its implicit derivatives (FP64), element by element, with d = s - beta u
+    of both signs and a few voxels on the guards (s <= 0, x e = 0)."""
+    from paper_2301_09710_gb300 import projector as pj
+    rng = np.random.default_rng(41)
+    n = 4099  # not a multiple of 4: the scalar path
+    x, e = rng.uniform(0.2, 3.0, n), rng.uniform(0.2, 3.0, n)
+    s, u, g = rng.uniform(0.5, 2.0, n), rng.uniform(0.0, 4.0, n), rng.normal(0, 1, n)
+    x[:5], e[5:10], s[10:15] = 0.0, 0.0, 0.0
+    f32 = [a.astype(np.float32) for a in (x, e, s, u, g)]
+    xd, ed, sd, ud, gd = (dev(a) for a in f32)
+    got = host(pj.em_update(xd, ed, sd, ud, beta))
+    x64, e64, s64, u64, g64 = (a.astype(np.float64) for a in f32)
+    want = oracle.em_root(x64, e64, s64, u64, beta)
+    assert_close(got, want, rel_l2=1e-6, max_rel=1e-5, what=f"EM update, beta={beta}")
+    gx, ge, gu = pj.em_update_backward(xd, ed, sd, ud, beta, gd)
+    wx, we, wu = oracle.em_root_vjp(x64, e64, s64, u64, beta, g64)
+    assert_close(host(gx), wx, rel_l2=1e-6, max_rel=1e-5, what=f"dL/dx, beta={beta}")
+    assert_close(host(ge), we, rel_l2=1e-6, max_rel=1e-5, what=f"dL/de, beta={beta}")
+    if beta > 0:
+        assert_close(host(gu), wu, rel_l2=1e-6, max_rel=1e-5, what=f"dL/du, beta={beta}")
+    else:
+        assert gu is None
+
+
+@pytest.mark.parametrize("n", [4096, 4097])
+def test_em_ratio_kernels_match_oracle(n):
+    from paper_2301_09710_gb300 import projector as pj
+    rng = np.random.default_rng(42)
+    ybar, y = rng.uniform(0.1, 5.0, n), rng.poisson(3.0, n).astype(np.float64)
+    rbar, g = rng.uniform(0.0, 0.5, n), rng.normal(0, 1, n)
+    ybar[:7] = -1.0  # ybar + rbar <= 0: ratio and gradient 0
+    f32 = [a.astype(np.float32) for a in (ybar, y, rbar, g)]
+    yb, yd, rd, gd = (dev(a) for a in f32)
+    b64 = [a.astype(np.float64) for a in f32]
+    assert_close(host(pj.em_ratio(yb, yd, rd)), oracle.em_ratio(*b64[:3]), rel_l2=1e-6, max_rel=1e-5,
+                 what="EM ratio")
+    assert_close(host(pj.em_ratio_backward(yb, yd, rd, gd)), oracle.em_ratio_vjp(*b64), rel_l2=1e-6, max_rel=1e-5,
+                 what="EM ratio gradient")
+    assert host(pj.em_ratio(yb, yd, None))[7:].tolist() == pytest.approx(
+        oracle.em_ratio(b64[0], b64[1])[7:].tolist(), rel=1e-6)
+
+
+def test_autograd_em_update_equals_fused_step():
+    """The differentiable EM update (A, the ratio kernel, A', the update kernel)
+    computes, step for step, the arithmetic of the fused regularised EM step:
+    bitwise the same image."""
+    from paper_2301_09710_gb300.autograd import em_update
+    prob, ang = _small()
+    plan = make_plan(prob, ang, "fused")
+    psf = oracle_psf(prob, "fused")
+    y = synthetic.poisson_counts(oracle.forward(prob.x, prob.mu, psf, prob.dy, ang) * 50, 2)
+    rbar = np.full_like(y, 0.1 * y.mean())
+    x0 = np.where(prob.body, 1.0, 0.0).astype(np.float32) + 0.1
+    u = np.random.default_rng(4).uniform(0.2, 3.0, x0.shape).astype(np.float32)
+    s = plan.sensitivity()
+    for beta in (0.0, 0.05, 5.0):
+        xg = dev(x0)
+        plan.em_step_reg(xg, dev(y), dev(u), beta, rbar=dev(rbar), niter=1)
+        with torch.no_grad():
+            xa = em_update(dev(x0), dev(y), dev(rbar), plan, s, dev(u), beta)
+        assert np.array_equal(host(xa), host(xg)), f"beta={beta}"
+    plan.check()

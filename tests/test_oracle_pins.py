@@ -595,3 +595,57 @@ def test_em3_preserves_counts_with_zero_background():
     for _ in range(2):
         x = oracle.em_step(x, y, None, prob.mu, psf, prob.dy, ang, s=s, rotation="3pass")
         assert abs(np.sum(s * x) - y.sum()) <= 1e-11 * y.sum()
+
+
+# ------------------------------------------------------------------ EM update gradients (Eqs. (7)-(8))
+def _central(f, x, h):
+    return (f(x + h) - f(x - h)) / (2.0 * h)
+
+
+@pytest.mark.parametrize("beta", [0.0, 0.05, 0.7, 30.0])
+def test_em_root_vjp_matches_finite_differences(beta):
+    """The implicit-function derivatives of the update (e/q, x/q, beta x+/q) against
+    central differences of em_root itself, element by element, at points where
+    d = s - beta u takes both signs (the two closed forms of the root)."""
+    rng = np.random.default_rng(31)
+    n = 400
+    x, e = rng.uniform(0.2, 3.0, n), rng.uniform(0.2, 3.0, n)
+    s, u = rng.uniform(0.5, 2.0, n), rng.uniform(0.0, 4.0, n)
+    if beta >= 0.5:  # both closed forms of the root are exercised
+        d = s - beta * u
+        assert (d > 0).any() and (d < 0).any()
+    g = rng.normal(0, 1, n)
+    gx, ge, gu = oracle.em_root_vjp(x, e, s, u, beta, g)
+    h = 1e-6
+    for got, var in ((gx, "x"), (ge, "e"), (gu, "u")):
+        def f(t):
+            args = {"x": x, "e": e, "u": u}
+            args[var] = t
+            return oracle.em_root(args["x"], args["e"], s, args["u"], beta)
+        want = g * _central(f, {"x": x, "e": e, "u": u}[var], h)
+        np.testing.assert_allclose(got, want, rtol=1e-6, atol=1e-9, err_msg=f"d/d{var}, beta={beta}")
+    if beta == 0:
+        assert not gu.any()
+
+
+def test_em_root_vjp_zero_where_the_guard_applies():
+    x, e = np.array([1.0, 2.0]), np.array([1.0, 0.0])
+    s, u = np.array([0.0, -1.0]), np.zeros(2)
+    gx, ge, gu = oracle.em_root_vjp(x, e, s, u, 0.0, np.ones(2))
+    assert not gx.any() and not ge.any() and not gu.any()
+    # beta > 0, d >= 0 with x e = 0 and d = 0: the root is 0 and so is the gradient
+    gx, ge, gu = oracle.em_root_vjp(np.array([0.0]), np.array([0.0]), np.array([1.0]), np.array([1.0]), 1.0,
+                                    np.ones(1))
+    assert gx[0] == ge[0] == gu[0] == 0
+
+
+def test_em_ratio_vjp_matches_finite_differences():
+    rng = np.random.default_rng(32)
+    n = 300
+    ybar, y, rbar, g = rng.uniform(0.5, 4, n), rng.poisson(3.0, n).astype(float), rng.uniform(0, 1, n), rng.normal(0, 1, n)
+    got = oracle.em_ratio_vjp(ybar, y, rbar, g)
+    want = g * _central(lambda t: oracle.em_ratio(t, y, rbar), ybar, 1e-6)
+    np.testing.assert_allclose(got, want, rtol=1e-6, atol=1e-9)
+    # guard: ybar + rbar <= 0 gives ratio 0 and gradient 0
+    assert oracle.em_ratio(np.array([-1.0]), np.array([2.0]), np.array([0.5]))[0] == 0
+    assert oracle.em_ratio_vjp(np.array([-1.0]), np.array([2.0]), np.array([0.5]), np.ones(1))[0] == 0
