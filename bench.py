@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default launch shapes")
     ap.add_argument("--serve-requests", type=int, default=160,
                     help="requests of the serving stream (20 req/s) timed served vs one at a time (0: skip)")
+    ap.add_argument("--train-steps", type=int, default=3,
+                    help="timed steps of the unrolled-EM training step reported beside (0: skip)")
+    ap.add_argument("--osem", type=int, default=1, help="time OSEM (4 subsets x 16 iterations) beside (0: skip)")
     ap.add_argument("--batch-plans", type=int, default=24,
                     help="reconstructions of the batching workload timed as one launch vs plan by plan (0: skip)")
     ap.add_argument("--nview", type=int, default=NVIEW,
@@ -406,8 +409,17 @@ def run_ours(args):
         batching = {"workload": b["workload"], "recon_per_s": b["recon_per_s"],
                     "speedup_vs_plan_by_plan": b["speedup_graph_tuned_vs_plain"],
                     "bitwise_equal_to_plan_by_plan": b["graph_bitwise_equal_to_plain"],
-                    "kernels_per_launch": b["kernels_per_graph_launch"], "times_s": {
+                    "kernels_per_launch": b["kernels_per_graph_launch"], "grouped_launches": b["grouped"],
+                    "times_s": {
                         k: b[k] for k in ("plain_s", "graph_s", "plain_tuned_s", "graph_tuned_s")}}
+
+    training = osem_line = None
+    if rank == 0 and world == 1 and args.train_steps > 0:
+        from paper_2301_09710_gb300 import autograd as ag
+        training = ag.run(outer=8, channels=8, beta=1.0, steps=args.train_steps)
+    if rank == 0 and world == 1 and args.osem > 0:
+        from paper_2301_09710_gb300 import osem as osm
+        osem_line = osm.run(4, 16)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -434,6 +446,10 @@ def run_ours(args):
             out["serving"] = serving
         if batching:
             out["batching"] = batching
+        if training:
+            out["training"] = training
+        if osem_line:
+            out["osem"] = osem_line
         if direct:
             out["direct_path"] = direct
         if rot3:

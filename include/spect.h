@@ -356,24 +356,38 @@ spect_status spect_plan_autotune(spect_plan plan, spect_stream stream);
 /*
  * Batches: many plans of different sizes, view counts and PSF widths run
  * their EM iterations as ONE CUDA graph launch (the paper has no
- * counterpart).  spect_batch_em_step captures, per plan, the same kernel
- * sequence spect_em_step would launch (niter iterations, transposes
- * included), each plan on its own branch of the graph so the plans' kernels
- * overlap on the device; the executable graph is cached and replayed while
- * niter and the pointer arrays' contents stay the same.
+ * counterpart).  By default spect_batch_em_step captures, per plan, the
+ * kernel sequence spect_em_step would launch (niter iterations, transposes
+ * included), each plan on its own branch of the graph, so the plans' kernels
+ * overlap on the device.  The executable graph is cached and replayed while
+ * niter, the pointer arrays' contents and the mode stay the same (a plan must
+ * not be retuned while it is in a batch).
  *   plans        n distinct plans; the batch borrows them (destroy the batch
  *                before its plans, and do not use the plans concurrently with
  *                the batch).
  *   x, y, rbar   HOST arrays of n DEVICE pointers (as spect_em_step; rbar may
  *                be NULL, or hold NULL entries).
  * Each plan's result is bitwise what spect_em_step gives for it alone.
- * spect_batch_info: plans in the batch and kernels per graph launch.
+ * spect_batch_set_grouped: with branches >= 1, and when every plan runs the
+ * fused separable-PSF kernels (the default for separable PSFs up to 37 taps),
+ * each stage of an EM iteration (rotation, blur + depth sums, reduce + ratio,
+ * blur adjoint, adjoint rotation + update) is instead ONE grouped launch per
+ * kernel variant over the blocks of every plan of a branch (at most 24 plans
+ * per launch; the plans split into `branches` branches of about equal work),
+ * so an iteration takes a handful of launches per branch whatever the number
+ * of plans; each plan still gets bitwise its own values.  For the grouped
+ * launches a plan processes every view in one pass: its work slab grows
+ * (stream-ordered) to hold every view, and stays so after the batch.  0 (the
+ * default) restores a graph branch per plan.  Errors: SPECT_EINVAL.
+ * spect_batch_info: plans in the batch and kernels per graph launch (after the
+ * first spect_batch_em_step).
  * Errors: SPECT_EINVAL, SPECT_ECUDA (capture or graph failures).
  */
 typedef struct spect_batch_s* spect_batch;
 spect_status spect_batch_create(spect_batch* out, const spect_plan* plans, int n);
 spect_status spect_batch_em_step(spect_batch batch, float* const* x, const float* const* y, const float* const* rbar,
                                  int niter, spect_stream stream);
+spect_status spect_batch_set_grouped(spect_batch batch, int branches);
 spect_status spect_batch_info(spect_batch batch, int* n_plans, long long* kernels_per_launch);
 spect_status spect_batch_destroy(spect_batch batch);
 

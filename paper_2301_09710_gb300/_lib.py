@@ -104,6 +104,8 @@ def load(path: str = LIB_PATH):
         lib.spect_batch_create.restype = st
         lib.spect_batch_em_step.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp]
         lib.spect_batch_em_step.restype = st
+        lib.spect_batch_set_grouped.argtypes = [vp, i]
+        lib.spect_batch_set_grouped.restype = st
         lib.spect_batch_info.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_longlong)]
         lib.spect_batch_info.restype = st
         lib.spect_batch_destroy.argtypes = [vp]

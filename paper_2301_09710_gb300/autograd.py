@@ -184,15 +184,24 @@ def main(argv=None):
     import argparse
     import json
 
-    import numpy as np
-
-    from . import synthetic
     ap = argparse.ArgumentParser(description="unrolled CNN-regularised EM: one training step")
     ap.add_argument("--outer", type=int, default=8)
     ap.add_argument("--channels", type=int, default=8)
     ap.add_argument("--beta", type=float, default=1.0)
     ap.add_argument("--steps", type=int, default=3)
     a = ap.parse_args(argv)
+    print(json.dumps(run(a.outer, a.channels, a.beta, a.steps)))
+
+
+def run(outer: int = 8, channels: int = 8, beta: float = 1.0, steps: int = 3) -> dict:
+    """One training step of the unrolled network at the paper's scale, timed with
+    CUDA events (median of `steps`), with and without checkpointing."""
+    import argparse
+
+    import numpy as np
+
+    from . import synthetic
+    a = argparse.Namespace(outer=outer, channels=channels, beta=beta, steps=steps)
     dev = torch.device("cuda")
     prob = synthetic.config2(seed=0)
     plan = SpectPlan(128, 80, 128, mu=prob.mu, dy=prob.dy, fx=prob.fx, fz=prob.fz, device=dev)
@@ -230,7 +239,8 @@ def main(argv=None):
         out[key] = {"ms_per_step": float(np.median(times)), "loss": loss.item(),
                     "peak_device_gb": torch.cuda.max_memory_allocated() / 2**30}
     plan.check()
-    print(json.dumps(out))
+    plan.close()
+    return out
 
 
 if __name__ == "__main__":

@@ -101,6 +101,17 @@ def run(n_plans: int = 24, niter: int = 8, reps: int = 3, seed: int = 0) -> dict
     same = all(torch.equal(x, r) for x, r in zip(xs, ref))
     kernels = batch.info()["kernels_per_launch"]
     batch.close()
+    # the same batch as grouped launches (one per stage and kernel variant over the
+    # blocks of every plan, in 1 and 4 branches), after the per-plan graph so its
+    # one-pass slabs do not change the plan-by-plan runs above
+    grouped = {}
+    for nbr in (1, 4):
+        batch = SpectBatch(plans, grouped=nbr)
+        batch.em_step(xs, ys, rbs, niter=a.niter)
+        tg = timed(lambda: batch.em_step(xs, ys, rbs, niter=a.niter))
+        grouped[nbr] = {"recon_per_s": len(plans) / tg, "s": tg,
+                        "kernels_per_graph_launch": batch.info()["kernels_per_launch"]}
+        batch.close()
     t1 = time.perf_counter()
     tunings = [pl.autotune() for pl in plans]
     tune_s = time.perf_counter() - t1
@@ -122,6 +133,7 @@ def run(n_plans: int = 24, niter: int = 8, reps: int = 3, seed: int = 0) -> dict
         "recon_per_s": {"plain": n / t_plain, "graph": n / t_graph, "graph_tuned": n / t_graph_tuned},
         "speedup_graph_tuned_vs_plain": t_plain / t_graph_tuned,
         "graph_bitwise_equal_to_plain": bool(same), "kernels_per_graph_launch": kernels,
+        "grouped": {f"branches_{k}": v for k, v in grouped.items()},
         "setup_s": setup_s, "autotune_s": tune_s, "tunings": tunings,
     })
 

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libspect.so")
 SOURCES = ["plan.cu", "rotate.cu", "conv.cu", "fused.cu", "gather.cu", "rotpatch.cu", "rot3.cu", "peak.cu",
-           "static_fwd.cu", "emupdate.cu"]
+           "static_fwd.cu", "emupdate.cu", "grouped.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills",
               "--expt-relaxed-constexpr"]

@@ -99,17 +99,17 @@ struct GatherArgs {
 // (per-stage "empty" barrier), so consumers never meet at a block barrier
 // inside the view loop.
 template <int MAXE>
-__global__ void __launch_bounds__(kGT + 32) k_adj_gather(const __grid_constant__ CUtensorMap tmap, GatherArgs a,
-                                                         const int4* __restrict__ boxes,
-                                                         const AdjEntry* __restrict__ pent, float* out,
-                                                         int accumulate, EmArgs em, int* err)
+__device__ __forceinline__ void adj_gather_body(const CUtensorMap* tmap, const GatherArgs& a,
+                                                const int4* __restrict__ boxes, const AdjEntry* __restrict__ pent,
+                                                float* out, int accumulate, const EmArgs& em, int* err,
+                                                const int patch, const int kcb)
 {
     extern __shared__ __align__(128) float sm[];
     const Geometry& g = a.g;
     uint64_t* full = reinterpret_cast<uint64_t*>(sm + (size_t)kStages * a.stage_floats);
     uint64_t* empty = full + kStages;
     volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kStages);
-    const int patch = blockIdx.x, kc0 = blockIdx.y * a.kc;
+    const int kc0 = kcb * a.kc;
     const int tid = threadIdx.x;
     const bool producer = tid >= kGT;
 
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kGT + 32) k_adj_gather(const __grid_constant__
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(full + s)),
                          "r"((unsigned)(a.box_floats * 4 + a.ent_bytes))
                          : "memory");
-            tma_load_3d(st, &tmap, kc0, b.x, v * g.ny + b.y, full + s);
+            tma_load_3d(st, tmap, kc0, b.x, v * g.ny + b.y, full + s);
             tma_copy_1d(st + a.box_floats, pent + ((size_t)patch * g.nview + l) * (kPatch * kPatch) * MAXE,
                         (unsigned)a.ent_bytes, full + s);
             issued = v + 1;
@@ -216,6 +216,15 @@ __global__ void __launch_bounds__(kGT + 32) k_adj_gather(const __grid_constant__
     }
 }
 
+template <int MAXE>
+__global__ void __launch_bounds__(kGT + 32) k_adj_gather(const __grid_constant__ CUtensorMap tmap, GatherArgs a,
+                                                         const int4* __restrict__ boxes,
+                                                         const AdjEntry* __restrict__ pent, float* out,
+                                                         int accumulate, EmArgs em, int* err)
+{
+    adj_gather_body<MAXE>(&tmap, a, boxes, pent, out, accumulate, em, err, blockIdx.x, blockIdx.y);
+}
+
 
 // floats per pipeline stage: the box, then the entries, rounded up to 128 bytes
 int stage_floats(int box_floats, int ent_bytes) { return (box_floats + ent_bytes / 4 + 31) & ~31; }
@@ -225,6 +234,31 @@ size_t gather_smem(int box_floats, int ent_bytes)
     // stages | full and empty barriers | abort flag
     return (size_t)kStages * stage_floats(box_floats, ent_bytes) * sizeof(float) + 2 * kStages * sizeof(uint64_t) +
            16;
+}
+
+// One plan's arguments of the grouped gather (the tensor map in the kernel's
+// parameter space, as in the per-plan launch).
+struct GroupGather {
+    CUtensorMap tmap;
+    GatherArgs a;
+    const int4* boxes;
+    const AdjEntry* pent;
+    float* out;
+    EmArgs em;
+    int accumulate;
+    int* err;
+};
+struct GroupGathers {
+    GroupGather p[kGroupMax];
+    GroupGrid grid;
+};
+
+template <int MAXE>
+__global__ void __launch_bounds__(kGT + 32) k_adj_gather_grp(const __grid_constant__ GroupGathers gg)
+{
+    const int4 w = group_item(gg.grid);
+    const GroupGather& q = gg.p[w.x];
+    adj_gather_body<MAXE>(&q.tmap, q.a, q.boxes, q.pent, q.out, q.accumulate, q.em, q.err, w.y, w.z);
 }
 
 }  // namespace
@@ -309,32 +343,45 @@ cudaError_t build_gather(spect_plan_s& P, cudaStream_t st)
     return e;
 }
 
+namespace {
+// The t slab as a 3D tensor map -- k (nz, contiguous) x i (nx, stride nz) x
+// plane (chunk * ny, stride ps) -- and the gather's arguments for views
+// [l0, l0 + nv).
+cudaError_t gather_setup(const spect_plan_s& P, int l0, int nv, CUtensorMap* map, GatherArgs* a)
+{
+    const Geometry& g = P.g;
+    const int kc = gather_kc();
+    const cuuint64_t dims[3] = {(cuuint64_t)g.nz, (cuuint64_t)g.nx, (cuuint64_t)P.chunk * g.ny};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.nz * 4, (cuuint64_t)P.ps * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)kc, (cuuint32_t)P.gbw, (cuuint32_t)P.gbh};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, P.slab, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    a->g = g;
+    a->npx = P.gnpx;
+    a->bw = P.gbw;
+    a->bh = P.gbh;
+    a->kc = kc;
+    a->box_floats = P.gbw * P.gbh * kc;
+    a->ent_bytes = kPatch * kPatch * P.adj_max * (int)sizeof(AdjEntry);
+    a->stage_floats = stage_floats(a->box_floats, a->ent_bytes);
+    a->l0 = l0;
+    a->nv = nv;
+    return cudaSuccess;
+}
+}  // namespace
+
 cudaError_t launch_adj_gather(const spect_plan_s& P, int l0, int nv, float* out, int accumulate, EmArgs em,
                               cudaStream_t st)
 {
     const Geometry& g = P.g;
     const int kc = gather_kc();
-    // the t slab as a 3D tensor: k (nz, contiguous) x i (nx, stride nz) x plane (chunk * ny, stride ps)
     CUtensorMap map;
-    const cuuint64_t dims[3] = {(cuuint64_t)g.nz, (cuuint64_t)g.nx, (cuuint64_t)P.chunk * g.ny};
-    const cuuint64_t strides[2] = {(cuuint64_t)g.nz * 4, (cuuint64_t)P.ps * 4};
-    const cuuint32_t box[3] = {(cuuint32_t)kc, (cuuint32_t)P.gbw, (cuuint32_t)P.gbh};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    if (encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, P.slab, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
     GatherArgs a;
-    a.g = g;
-    a.npx = P.gnpx;
-    a.bw = P.gbw;
-    a.bh = P.gbh;
-    a.kc = kc;
-    a.box_floats = P.gbw * P.gbh * kc;
-    a.ent_bytes = kPatch * kPatch * P.adj_max * (int)sizeof(AdjEntry);
-    a.stage_floats = stage_floats(a.box_floats, a.ent_bytes);
-    a.l0 = l0;
-    a.nv = nv;
+    cudaError_t es = gather_setup(P, l0, nv, &map, &a);
+    if (es != cudaSuccess) return es;
     const size_t smem = gather_smem(a.box_floats, a.ent_bytes);
     const dim3 grid(P.gnpx * P.gnpy, (g.nz + kc - 1) / kc);
     switch (P.adj_max) {
@@ -351,6 +398,71 @@ cudaError_t launch_adj_gather(const spect_plan_s& P, int l0, int nv, float* out,
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+// The grouped gather of a batch: per adjacency-list length, one launch over
+// every plan's (patch, k run) blocks, largest plans first; each plan's MLEM
+// update (beta = 0) in the epilogue, as in its own EM step.
+cudaError_t build_grouped_gather(const std::vector<spect_plan_s*>& plans, GroupedBatch& B,
+                                 std::vector<GroupLaunch>& out)
+{
+    (void)B;
+    for (int maxe = 1; maxe <= 8; ++maxe) {
+        std::vector<int> idx;
+        for (int i = 0; i < (int)plans.size(); ++i)
+            if (plans[i]->adj_max == maxe) idx.push_back(i);
+        std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+            const auto w = [](const spect_plan_s* P) { return (size_t)P->g.nx * P->g.ny * P->g.nz * P->g.nview; };
+            return w(plans[x]) > w(plans[y]);
+        });
+        for (size_t c0 = 0; c0 < idx.size(); c0 += kGroupMax) {
+            const size_t c1 = std::min(idx.size(), c0 + (size_t)kGroupMax);
+            GroupGathers gg{};
+            size_t smem = 0;
+            for (size_t m = c0; m < c1; ++m) {
+                const spect_plan_s& P = *plans[idx[m]];
+                GroupGather& q = gg.p[m - c0];
+                cudaError_t e = gather_setup(P, 0, P.g.nview, &q.tmap, &q.a);
+                if (e != cudaSuccess) return e;
+                q.boxes = P.gboxes;
+                q.pent = P.gent;
+                q.out = P.et;
+                q.em.x = P.xt;
+                q.em.s = P.st;
+                q.em.u = nullptr;
+                q.em.beta = 0.f;
+                q.accumulate = 0;
+                q.err = P.err;
+                smem = std::max(smem, gather_smem(q.a.box_floats, q.a.ent_bytes));
+                // the gather's grid: (patch, run of kc depth rows)
+                const int mm = (int)(m - c0), nkc = (P.g.nz + q.a.kc - 1) / q.a.kc;
+                if (mm == 0) gg.grid.first[0] = 0;
+                gg.grid.gx[mm] = P.gnpx * P.gnpy;
+                gg.grid.gy[mm] = nkc;
+                gg.grid.first[mm + 1] = gg.grid.first[mm] + P.gnpx * P.gnpy * nkc;
+                gg.grid.n = mm + 1;
+            }
+            const unsigned nb = (unsigned)gg.grid.first[gg.grid.n];
+            GroupLaunch L;
+            switch (maxe) {
+#define SPECT_GG(M)                                                                                            \
+    case M:                                                                                                    \
+        L = [gg, nb, smem](cudaStream_t st) -> cudaError_t {                                                   \
+            cudaError_t e2 = cudaFuncSetAttribute(k_adj_gather_grp<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                                  (int)smem);                                                  \
+            if (e2 != cudaSuccess) return e2;                                                                  \
+            k_adj_gather_grp<M><<<nb, kGT + 32, smem, st>>>(gg);                                                \
+            return cudaGetLastError();                                                                         \
+        };                                                                                                     \
+        break;
+                SPECT_GG(1) SPECT_GG(2) SPECT_GG(3) SPECT_GG(4) SPECT_GG(5) SPECT_GG(6) SPECT_GG(7) SPECT_GG(8)
+#undef SPECT_GG
+                default: return cudaErrorInvalidValue;
+            }
+            out.push_back(L);
+        }
+    }
+    return cudaSuccess;
 }
 
 }  // namespace spect

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <numeric>
 #include <cstdlib>
 #include <map>
 #include <mutex>
@@ -890,6 +891,12 @@ struct spect_batch_s {
     cudaGraphExec_t exec = nullptr;
     std::vector<const void*> key;
     long long graph_launches = 0;   // kernels per graph launch
+    // grouped launches (every plan on the fused separable path): the plans split
+    // into a few branches of about equal work; on each branch one launch per
+    // stage and kernel variant over the branch's plans
+    std::vector<spect::GroupedBatch> grouped;
+    int grouped_on = 0;
+    int grouped_branches = 0;  // spect_batch_set_grouped: 0 = a graph branch per plan
 };
 
 namespace {
@@ -952,6 +959,23 @@ spect_status reconfigure(spect_plan_s* P, int J, int adj_J, int tiles, cudaStrea
     }
     P->chunk = chunk;
     P->adj_chunk = P->adj_chunk_req > 0 ? std::min(P->adj_chunk_req, chunk) : chunk;
+    return SPECT_OK;
+}
+
+// One pass over every view, as the grouped batch launches need: grow the work
+// slab (stream-ordered on st) so it holds every view of a fused separable plan.
+spect_status single_pass(spect_plan_s* P, cudaStream_t st)
+{
+    if (!P->fast || !P->separable || P->rot3) return SPECT_OK;
+    const Geometry& g = P->g;
+    if (P->chunk >= g.nview && P->adj_chunk >= g.nview) return SPECT_OK;
+    if (P->adj_chunk_req > 0 && P->adj_chunk_req < g.nview) return SPECT_OK;  // adjoint passes asked for
+    const size_t vol = (size_t)g.nx * g.ny * g.nz;
+    const size_t per_view = std::max(vol, spect::fused_slab_per_view(*P));
+    spect_status r = realloc_floats(P, &P->slab, &P->slab_cap, per_view * (size_t)g.nview, st, "work slab");
+    if (r != SPECT_OK) return r;
+    P->chunk = g.nview;
+    P->adj_chunk = g.nview;
     return SPECT_OK;
 }
 
@@ -1147,6 +1171,59 @@ spect_status spect_batch_em_step(spect_batch B, float* const* x, const float* co
     if (!B->exec || key != B->key) {
         if (B->exec) cudaGraphExecDestroy(B->exec);
         B->exec = nullptr;
+        // grouped launches when every plan runs the fused separable kernels in one
+        // pass (SPECT_BATCH_GROUPED=0, testing: a graph branch per plan instead)
+        for (spect::GroupedBatch& gb : B->grouped) spect::free_grouped(gb);
+        B->grouped.clear();
+        B->grouped_on = 0;
+        bool grp = B->grouped_branches > 0;
+        for (spect_plan_s* P : B->plans) {
+            if (!grp) break;
+            if (single_pass(P, st) != SPECT_OK) {  // no room for every view: a graph branch per plan
+                cudaGetLastError();
+                grp = false;
+            }
+            grp = grp && spect::groupable(*P);
+        }
+        if (grp) {
+            // branches: longest-processing-time assignment of the plans by work
+            const int nbr = std::min(B->grouped_branches, std::min(n, (int)B->side.size()));
+            std::vector<int> order(n);
+            std::iota(order.begin(), order.end(), 0);
+            auto work = [&](int i) {
+                const Geometry& g = B->plans[i]->g;
+                return (double)g.nx * g.ny * g.nz * g.nview;
+            };
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+            std::vector<std::vector<int>> members(nbr);
+            std::vector<double> load(nbr, 0.0);
+            for (int i : order) {
+                const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+                members[b].push_back(i);
+                load[b] += work(i);
+            }
+            B->grouped.resize(nbr);
+            cudaError_t eg = cudaSuccess;
+            for (int b = 0; b < nbr && eg == cudaSuccess; ++b) {
+                std::vector<spect_plan_s*> pl;
+                std::vector<float*> xb;
+                std::vector<const float*> yb, rb;
+                for (int i : members[b]) {
+                    pl.push_back(B->plans[i]);
+                    xb.push_back(x[i]);
+                    yb.push_back(y[i]);
+                    rb.push_back(rbar ? rbar[i] : nullptr);
+                }
+                eg = spect::build_grouped(pl, xb.data(), yb.data(), rb.data(), B->grouped[b]);
+            }
+            if (eg != cudaSuccess) {
+                for (spect::GroupedBatch& gb : B->grouped) spect::free_grouped(gb);
+                B->grouped.clear();
+                cudaGetLastError();
+                return fail(SPECT_ECUDA, std::string("grouped batch set-up: ") + cudaGetErrorString(eg));
+            }
+            B->grouped_on = 1;
+        }
         std::vector<int> prof(n);
         std::vector<long long> before(n);
         for (int i = 0; i < n; ++i) {
@@ -1163,7 +1240,27 @@ spect_status spect_batch_em_step(spect_batch B, float* const* x, const float* co
         const int ns = (int)B->side.size();
         for (int s = 0; s < ns && e == cudaSuccess; ++s) e = cudaStreamWaitEvent(B->side[s], B->fork, 0);
         if (r == SPECT_OK && e != cudaSuccess) r = fail(SPECT_ECUDA, std::string("fork: ") + cudaGetErrorString(e));
-        for (int i = 0; i < n && r == SPECT_OK; ++i)
+        long long grouped_kernels = 0;
+        if (B->grouped_on) {
+            // one chain per branch: layouts in, niter x (rotation, blur, reduce +
+            // ratio, blur adjoint, gather + update), layouts out
+            for (size_t b = 0; b < B->grouped.size() && r == SPECT_OK; ++b) {
+                cudaStream_t bs = B->side[b];
+                auto run = [&](const std::vector<spect::GroupLaunch>& L) {
+                    for (const spect::GroupLaunch& f : L) {
+                        if (r != SPECT_OK) return;
+                        const cudaError_t el = f(bs);
+                        if (el != cudaSuccess)
+                            r = fail(SPECT_ECUDA, std::string("grouped launch: ") + cudaGetErrorString(el));
+                        ++grouped_kernels;
+                    }
+                };
+                run(B->grouped[b].head);
+                for (int it = 0; it < niter; ++it) run(B->grouped[b].iter);
+                run(B->grouped[b].tail);
+            }
+        }
+        for (int i = 0; i < n && r == SPECT_OK && !B->grouped_on; ++i)
             r = em_iterate(B->plans[i], x[i], y[i], rbar ? rbar[i] : nullptr, nullptr, 0.f, niter, B->side[i % ns]);
         for (int s = 0; s < ns && r == SPECT_OK; ++s) {
             e = cudaEventRecord(B->join[s], B->side[s]);
@@ -1190,11 +1287,22 @@ spect_status spect_batch_em_step(spect_batch B, float* const* x, const float* co
         }
         cudaGetLastError();
         if (r != SPECT_OK) return r;
-        B->graph_launches = total;
+        B->graph_launches = B->grouped_on ? grouped_kernels : total;
         B->key = key;
     }
     cudaError_t e = cudaGraphLaunch(B->exec, st);
     if (e != cudaSuccess) return fail(SPECT_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    return SPECT_OK;
+}
+
+spect_status spect_batch_set_grouped(spect_batch B, int branches)
+{
+    if (!B) return fail(SPECT_EINVAL, "batch is NULL");
+    if (branches < 0 || branches > 32) return fail(SPECT_EINVAL, "branches must be in [0, 32]");
+    if (branches != B->grouped_branches) {
+        B->grouped_branches = branches;
+        B->key.clear();  // captured again on the next call
+    }
     return SPECT_OK;
 }
 
@@ -1215,6 +1323,11 @@ spect_status spect_batch_destroy(spect_batch B)
         if (e == cudaSuccess) e = e1;
     }
     if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->origin) {
+        cudaError_t e1 = cudaStreamSynchronize(B->origin);
+        if (e == cudaSuccess) e = e1;
+    }
+    for (spect::GroupedBatch& gb : B->grouped) spect::free_grouped(gb);
     for (cudaStream_t s : B->side) cudaStreamDestroy(s);
     if (B->origin) cudaStreamDestroy(B->origin);
     for (cudaEvent_t j : B->join) cudaEventDestroy(j);

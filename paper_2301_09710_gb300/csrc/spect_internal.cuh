@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -384,6 +385,38 @@ cudaError_t launch_adj_gather(const spect_plan_s& P, int l0, int nv, float* out,
 cudaError_t launch_adj_rot_t(const spect_plan_s& P, int l0, int nv, float* out, int accumulate, EmArgs em,
                              cudaStream_t st);
 bool direct_fits(const Geometry& g, size_t smem_limit);
+// grouped launches of a batch of plans (grouped.cu, gather.cu): per stage and
+// kernel variant one launch over a work list spanning the plans (at most
+// kGroupMax plans per launch); head / iter / tail: layouts in, one EM
+// iteration, layouts out
+constexpr int kGroupMax = 24;
+// Where each plan's blocks sit in a grouped launch: plan m owns blocks
+// [first[m], first[m+1]) laid out as its own grid (gx x gy x gz, x fastest),
+// so a block finds its plan and coordinates from blockIdx.x alone.
+struct GroupGrid {
+    int n;
+    int first[kGroupMax + 1];
+    int gx[kGroupMax], gy[kGroupMax];
+};
+__device__ __forceinline__ int4 group_item(const GroupGrid& gg)
+{
+    const int b = (int)blockIdx.x;
+    int m = 0;
+    while (m + 1 < gg.n && b >= gg.first[m + 1]) ++m;
+    const int r = b - gg.first[m], gx = gg.gx[m], gy = gg.gy[m];
+    const int q = r / gx;
+    return make_int4(m, r - q * gx, q % gy, q / gy);
+}
+using GroupLaunch = std::function<cudaError_t(cudaStream_t)>;
+struct GroupedBatch {
+    std::vector<GroupLaunch> head, iter, tail;
+};
+bool groupable(const spect_plan_s& P);
+cudaError_t build_grouped(const std::vector<spect_plan_s*>& plans, float* const* x, const float* const* y,
+                          const float* const* rbar, GroupedBatch& B);
+cudaError_t build_grouped_gather(const std::vector<spect_plan_s*>& plans, GroupedBatch& B,
+                                 std::vector<GroupLaunch>& out);
+void free_grouped(GroupedBatch& B);
 cudaError_t launch_fill(float* p, size_t n, float value, cudaStream_t st);
 
 }  // namespace spect

@@ -74,11 +74,20 @@ def main(argv=None):
     import argparse
     import json
 
-    from . import synthetic
     ap = argparse.ArgumentParser(description="OSEM reconstruction timing")
     ap.add_argument("--subsets", type=int, default=4)
     ap.add_argument("--iters", type=int, default=16)
     a = ap.parse_args(argv)
+    print(json.dumps(run(a.subsets, a.iters)))
+
+
+def run(subsets: int = 4, iters: int = 16) -> dict:
+    """OSEM (subsets x iters) against `iters` MLEM iterations on the paper-scale
+    workload, timed with CUDA events after a warm-up run."""
+    import argparse
+
+    from . import synthetic
+    a = argparse.Namespace(subsets=subsets, iters=iters)
     prob = synthetic.config2(seed=0)
     full = SpectPlan(128, 80, 128, mu=prob.mu, dy=prob.dy, fx=prob.fx, fz=prob.fz)
     xt = torch.from_numpy(prob.x).cuda()
@@ -106,7 +115,9 @@ def main(argv=None):
         out[name] = {"s": e0.elapsed_time(e1) / 1e3, "nrmsd_to_phantom": err}
     os_.check()
     full.check()
-    print(json.dumps(out))
+    os_.close()
+    full.close()
+    return out
 
 
 if __name__ == "__main__":

@@ -314,16 +314,23 @@ class SpectPlan:
 
 
 class SpectBatch:
-    """Plans of different sizes whose EM iterations run as one CUDA graph launch
-    (one graph branch per plan; see spect_batch_em_step)."""
+    """Plans of different sizes whose EM iterations run as one CUDA graph launch:
+    one graph branch per plan (grouped=0), or grouped launches -- one per stage and
+    kernel variant over the blocks of every plan -- in `grouped` branches
+    (spect_batch_em_step, spect_batch_set_grouped)."""
 
-    def __init__(self, plans):
+    def __init__(self, plans, grouped: int = 0):
         self.lib = _lib.load()
         self.plans = list(plans)
         arr = (ctypes.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
         handle = ctypes.c_void_p()
         _lib.check(self.lib.spect_batch_create(ctypes.byref(handle), arr, len(self.plans)))
         self.handle = handle
+        if grouped:
+            self.set_grouped(grouped)
+
+    def set_grouped(self, branches: int) -> None:
+        _lib.check(self.lib.spect_batch_set_grouped(self.handle, int(branches)))
 
     def em_step(self, xs, ys, rbars=None, niter: int = 1, stream=None):
         """niter MLEM updates of every plan's x in place (xs, ys, rbars: lists of CUDA tensors)."""

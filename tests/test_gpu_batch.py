@@ -116,3 +116,67 @@ def test_autotune_picks_a_valid_shape_and_caches_it():
     # a low-memory plan has nothing to tune
     p3 = make_plan(prob, ang, "lowmem")
     p3.autotune()
+
+
+# every plan on the fused separable kernels: the batch runs as grouped launches
+FUSED_MIX = [(24, 8, 12, 5, 11), (33, 12, 16, 11, 12), (40, 8, 9, 7, 13), (48, 16, 14, 21, 14), (56, 20, 10, 9, 15),
+             (40, 12, 11, 5, 16)]
+
+
+def _fused_batch_inputs():
+    out = []
+    for nx, nz, nv, p, seed in FUSED_MIX:
+        prob = synthetic.config1(seed=seed, nx=nx, nz=nz, nview=nv, psf_size=p)
+        ang = oracle.default_angles(nv)
+        psf = oracle_psf(prob, "fused")
+        y = synthetic.poisson_counts(oracle.forward(prob.x, prob.mu, psf, prob.dy, ang) * 20, seed)
+        rbar = np.full_like(y, 0.1 * float(y.mean()) + 0.01)
+        x0 = np.where(prob.body, 1.0, 0.0).astype(np.float32) + 0.05
+        out.append((prob, ang, psf, y, rbar, x0))
+    return out
+
+
+@pytest.mark.parametrize("branches", [1, 3])
+def test_grouped_batch_equals_each_plan_alone(branches):
+    """A batch whose plans all run the fused separable kernels runs each EM stage as
+    one grouped launch over every plan (work items from all plans, the plans'
+    arguments in the launch's parameters): fewer launches than a graph branch per
+    plan, and every plan's iterates bitwise those of the plan alone and of the
+    per-plan graph -- uneven sizes, view counts, five PSF buckets and a
+    column-tiled plan."""
+    from paper_2301_09710_gb300 import SpectBatch
+    probs = _fused_batch_inputs()
+    plans = [make_plan(pr, ang, "fused") for pr, ang, *_ in probs]
+    t = plans[-1].tuning
+    plans[-1].set_tuning(t["fused_J"], t["adj_J"], 2)  # column tiles: the tiled kernel variants
+    assert plans[-1].tuning["tiles"] > 1
+    ys = [dev(y) for _, _, _, y, _, _ in probs]
+    rbs = [dev(rb) for _, _, _, _, rb, _ in probs]
+    niter = 3
+    runs = {}
+    for mode in ("1", "0"):
+        batch = SpectBatch(plans, grouped=branches if mode == "1" else 0)
+        xs = [dev(x0) for *_, x0 in probs]
+        batch.em_step(xs, ys, rbs, niter=niter)
+        first = [host(x) for x in xs]
+        for x, (*_, x0) in zip(xs, probs):
+            x.copy_(dev(x0))
+        batch.em_step(xs, ys, rbs, niter=niter)  # replayed
+        runs[mode] = (first, [host(x) for x in xs], batch.info()["kernels_per_launch"])
+        batch.close()
+    assert runs["1"][2] < runs["0"][2], (runs["1"][2], runs["0"][2])
+    for i, (pl, (pr, ang, psf, y, rb, x0)) in enumerate(zip(plans, probs)):
+        xa = dev(x0)
+        pl.em_step(xa, ys[i], rbs[i], niter=niter)
+        alone = host(xa)
+        for mode in ("1", "0"):
+            assert np.array_equal(runs[mode][0][i], alone), f"plan {i}, grouped={mode}: differs from the plan alone"
+            assert np.array_equal(runs[mode][1][i], alone), f"plan {i}, grouped={mode}: replay differs"
+        if i < 2:
+            s = oracle.sensitivity(pr.mu, psf, pr.dy, ang)
+            xo = x0.astype(np.float64)
+            for _ in range(niter):
+                xo = oracle.em_step(xo, y, rb, pr.mu, psf, pr.dy, ang, s=s)
+            assert_close(alone, xo, rel_l2=1e-5, max_rel=1e-3, what=f"plan {i} EM iterates vs oracle")
+        pl.check()
+        pl.close()
