@@ -46,39 +46,58 @@ cudaError_t launch_transpose(const float* in, float* out, int R, int C, cudaStre
 }
 
 // mubar[l][j][i][k] = exp(-dy (mu~(j)/2 + sum_{s>j} mu~(s))), Eq. (1), for every
-// view; one thread per (l, i, k) walking j from the detector side.  mu_t is mu
-// in the [j][i][k] layout; planes (l, j) are ps floats apart (16-byte aligned
-// for bulk copies).
-__global__ void k_mubar_cache(Geometry g, int ps, const ViewRot* __restrict__ rot, const float* __restrict__ mu_t,
-                              float* __restrict__ mubar)
+// view.  One block per (32 columns k, row i, view l) walks depth from the
+// detector side in tiles of 32 depths: the rotated mu~ of the tile is gathered
+// with lanes over k (coalesced), each warp then scans its four columns along
+// depth (atten_warp_scan, lanes over depth), and the factors leave with lanes
+// over k again.  mu_t is mu in the [j][i][k] layout; planes (l, j) are ps floats
+// apart (16-byte aligned for bulk copies).
+__global__ void __launch_bounds__(256) k_mubar_cache(Geometry g, int ps, const ViewRot* __restrict__ rot,
+                                                     const float* __restrict__ mu_t, float* __restrict__ mubar)
 {
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t per_view = (size_t)g.nx * g.nz;
-    if (idx >= per_view * g.nview) return;
-    const int l = (int)(idx / per_view);
-    const int rem = (int)(idx - (size_t)l * per_view);
-    const int i = rem / g.nz, k = rem - i * g.nz;
+    __shared__ float tile[32][33];
+    const int kc = blockIdx.x, i = blockIdx.y, l = blockIdx.z;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k = kc * 32 + lane;
     const ViewRot r = rot[l];
-    AttenScan sc;
-    for (int j = g.ny - 1; j >= 0; --j) {
-        float4 w;
-        int base;
-        rot_table_entry(i, j, r, g, w, base);
-        const float* m = mu_t + (size_t)base * g.nz + k;
-        const size_t rs = (size_t)g.nx * g.nz;
-        float mv = 0.f;
-        mv = __fmaf_rn(w.x, m[0], mv);
-        mv = __fmaf_rn(w.y, m[g.nz], mv);
-        mv = __fmaf_rn(w.z, m[rs], mv);
-        mv = __fmaf_rn(w.w, m[rs + g.nz], mv);
-        mubar[((size_t)l * g.ny + j) * ps + (size_t)i * g.nz + k] = g.has_mu ? sc.step(mv, g.dy) : 1.f;
+    const size_t rs = (size_t)g.nx * g.nz;
+    DFloat carry[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};  // columns warp + 8t
+    for (int j0 = g.ny - 1; j0 >= 0; j0 -= 32) {  // depths j0, j0-1, ..., j0-31
+        for (int q = warp; q < 32; q += 8) {
+            const int j = j0 - q;
+            float mv = 0.f;
+            if (j >= 0 && k < g.nz) {
+                float4 w;
+                int base;
+                rot_table_entry(i, j, r, g, w, base);
+                const float* m = mu_t + (size_t)base * g.nz + k;
+                mv = __fmaf_rn(w.x, m[0], mv);
+                mv = __fmaf_rn(w.y, m[g.nz], mv);
+                mv = __fmaf_rn(w.z, m[rs], mv);
+                mv = __fmaf_rn(w.w, m[rs + g.nz], mv);
+            }
+            tile[q][lane] = mv;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int c = warp + 8 * t;
+            const float m = tile[lane][c];
+            tile[lane][c] = g.has_mu ? atten_warp_scan(m, carry[t], g.dy) : 1.f;
+        }
+        __syncthreads();
+        for (int q = warp; q < 32; q += 8) {
+            const int j = j0 - q;
+            if (j >= 0 && k < g.nz) mubar[((size_t)l * g.ny + j) * ps + (size_t)i * g.nz + k] = tile[q][lane];
+        }
+        __syncthreads();
     }
 }
 
 cudaError_t launch_mubar_cache(const spect_plan_s& P, const float* mu_t, cudaStream_t st)
 {
-    const size_t n = (size_t)P.g.nx * P.g.nz * P.g.nview;
-    k_mubar_cache<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.g, P.ps, P.rot, mu_t, P.mubar);
+    const dim3 grid((P.g.nz + 31) / 32, P.g.nx, P.g.nview);
+    k_mubar_cache<<<grid, 256, 0, st>>>(P.g, P.ps, P.rot, mu_t, P.mubar);
     return cudaGetLastError();
 }
 

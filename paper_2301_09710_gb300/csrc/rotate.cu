@@ -8,39 +8,61 @@
 namespace spect {
 
 // ----------------------------------------------------------------------------
-// K1: w(i,j,k; v) = x~(i,j,k) * mubar(i,j,k), one thread per (i,k) column of
-// one view, walking depth from the detector side (j = ny-1) inwards so the
-// Eq. (1) sum over s > j is a running (compensated) sum.
+// K1: w(i,j,k; v) = x~(i,j,k) * mubar(i,j,k), rotation and Eq. (1) attenuation
+// fused.  One block per (32 columns i, slice k, view): it walks depth from the
+// detector side in tiles of 32 depths; per tile the rotated x~ and mu~ are
+// gathered with lanes over i, each warp scans four columns of mu~ along depth
+// (atten_warp_scan, lanes over depth) into the factors mubar, and w = x~ mubar
+// leaves with lanes over i (coalesced rows of the slab).
 // Output: slab[v][k][j][i].
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_rotate_atten(Geometry g, const ViewRot* __restrict__ rot,
+__global__ void __launch_bounds__(256) k_rotate_atten(Geometry g, const ViewRot* __restrict__ rot,
                                                       const float* __restrict__ x, const float* __restrict__ mu,
                                                       float* __restrict__ slab, int l0)
 {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    const int v = blockIdx.y;
-    if (idx >= g.nx * g.nz) return;
-    const int i = idx % g.nx, k = idx / g.nx;
+    __shared__ float tx[32][33], tm[32][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane, k = blockIdx.y, v = blockIdx.z;
     const ViewRot r = rot[l0 + v];
     const size_t nxy = (size_t)g.nx * g.ny;
     const float* xs = x + (size_t)k * nxy;
     const float* ms = mu + (size_t)k * nxy;
-    float* out = slab + ((size_t)v * g.nz + k) * nxy + i;
-    AttenScan sc;
-    for (int j = g.ny - 1; j >= 0; --j) {
-        const Sample s = rot_sample(i, j, r, g.cint, g.cfrac);
-        const float xv = gather_bilinear(xs, s, g.nx, g.ny);
-        float mb = 1.f;
-        if (g.has_mu) mb = sc.step(gather_bilinear(ms, s, g.nx, g.ny), g.dy);
-        out[(size_t)j * g.nx] = xv * mb;
+    float* out = slab + ((size_t)v * g.nz + k) * nxy;
+    DFloat carry[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};  // columns warp + 8t
+    for (int j0 = g.ny - 1; j0 >= 0; j0 -= 32) {  // depths j0, j0-1, ..., j0-31
+        for (int q = warp; q < 32; q += 8) {
+            const int j = j0 - q;
+            float xv = 0.f, mv = 0.f;
+            if (j >= 0 && i < g.nx) {
+                const Sample s = rot_sample(i, j, r, g.cint, g.cfrac);
+                xv = gather_bilinear(xs, s, g.nx, g.ny);
+                if (g.has_mu) mv = gather_bilinear(ms, s, g.nx, g.ny);
+            }
+            tx[q][lane] = xv;
+            tm[q][lane] = mv;
+        }
+        __syncthreads();
+        if (g.has_mu) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int c = warp + 8 * t;
+                tx[lane][c] *= atten_warp_scan(tm[lane][c], carry[t], g.dy);
+            }
+        }
+        __syncthreads();
+        for (int q = warp; q < 32; q += 8) {
+            const int j = j0 - q;
+            if (j >= 0 && i < g.nx) out[(size_t)j * g.nx + i] = tx[q][lane];
+        }
+        __syncthreads();
     }
 }
 
 cudaError_t launch_rotate_atten(const spect_plan_s& P, const float* x, int l0, int nv, cudaStream_t st)
 {
     const Geometry& g = P.g;
-    dim3 grid((g.nx * g.nz + 127) / 128, nv);
-    k_rotate_atten<<<grid, 128, 0, st>>>(g, P.rot, x, P.mu, P.slab, l0);
+    dim3 grid((g.nx + 31) / 32, g.nz, nv);
+    k_rotate_atten<<<grid, 256, 0, st>>>(g, P.rot, x, P.mu, P.slab, l0);
     return cudaGetLastError();
 }
 

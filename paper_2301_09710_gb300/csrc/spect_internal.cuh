@@ -189,6 +189,47 @@ __device__ __forceinline__ float gather_bilinear(const float* __restrict__ sl, c
 
 // Running Eq. (1) attenuation along depth, from the detector side (j = ny-1)
 // inwards: S = sum_{s>j} mu~(s) kept with Kahan compensation.
+// Eq. (1) as a warp scan along depth.  Lane q of the warp holds mu~ of the
+// q-th of 32 consecutive depths counted from the detector side; `carry` is the
+// sum of mu~ over every depth nearer the detector (a double-float pair).  The
+// inclusive prefix sums over the lanes are formed in five shuffle steps with
+// compensated (two-sum) additions, so the sum S of Eq. (1) keeps about twice
+// FP32's precision however many depths it spans; the lane's factor is
+// exp(-dy (S + mu~/2)) with S the sum over the depths before it.  carry
+// advances past the 32 depths.  Every lane of the warp must call it.
+struct DFloat {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DFloat df_add(DFloat a, DFloat b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = ((a.hi - (s - bb)) + (b.hi - bb)) + (a.lo + b.lo);
+    const float hi = s + e;
+    return {hi, e - (hi - s)};
+}
+
+__device__ __forceinline__ float atten_warp_scan(float m, DFloat& carry, float dy)
+{
+    const int lane = threadIdx.x & 31;
+    DFloat inc = {m, 0.f};
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const DFloat o = {__shfl_up_sync(0xffffffffu, inc.hi, d), __shfl_up_sync(0xffffffffu, inc.lo, d)};
+        if (lane >= d) inc = df_add(o, inc);
+    }
+    DFloat ex = {__shfl_up_sync(0xffffffffu, inc.hi, 1), __shfl_up_sync(0xffffffffu, inc.lo, 1)};
+    if (lane == 0) ex = {0.f, 0.f};
+    const DFloat sum = df_add(carry, ex);
+    const float mb = expf(-dy * (sum.hi + (sum.lo + 0.5f * m)));
+    const DFloat tot = {__shfl_sync(0xffffffffu, inc.hi, 31), __shfl_sync(0xffffffffu, inc.lo, 31)};
+    carry = df_add(carry, tot);
+    return mb;
+}
+
+// Eq. (1) walked serially from the detector side with a compensated running
+// sum (the low-memory blur adjoints, which visit depths one at a time).
 struct AttenScan {
     float S = 0.f, c = 0.f;
     // mubar(j) = exp(-dy (mu~(j)/2 + S)), then S += mu~(j)
