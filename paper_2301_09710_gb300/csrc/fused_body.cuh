@@ -400,6 +400,16 @@ __device__ __forceinline__ void fwd_sep_body(const Geometry& g, const FusedDims&
     // tile `tile` of plane j sits at wv + j * parea
     const float* wv = wsl + (size_t)v * ny * d.parea + (size_t)tile * d.warea;
 
+    // the first two plane images are requested before anything else, so their
+    // loads overlap the set-up below
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tma_load_1d(WB, wv + (size_t)j_begin * d.parea, (unsigned)d.warea * 4u, bar);
+        if (j_begin + 1 < j_end)
+            tma_load_1d(WB + d.warea, wv + (size_t)(j_begin + 1) * d.parea, (unsigned)d.warea * 4u, bar + 1);
+    }
     // taps of every plane of the group (zero-padded to P, centred)
     for (int e = tid; e < (j_end - j_begin) * PT; e += T) {
         const int jj = e / PT, a = e - jj * PT, j = j_begin + jj;
@@ -409,14 +419,6 @@ __device__ __forceinline__ void fwd_sep_body(const Geometry& g, const FusedDims&
     }
     for (int e = tid; e < d.urows * d.apc; e += T) ACC[e] = 0.f;
     for (int e = tid; e < d.urows * d.kpu; e += T) U[e] = 0.f;  // zero k-halo columns (never written again)
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        mbar_init(bar + 1, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        tma_load_1d(WB, wv + (size_t)j_begin * d.parea, (unsigned)d.warea * 4u, bar);
-        if (j_begin + 1 < j_end)
-            tma_load_1d(WB + d.warea, wv + (size_t)(j_begin + 1) * d.parea, (unsigned)d.warea * 4u, bar + 1);
-    }
     __syncthreads();
     // replicate padding along k, folded: output k takes U(0) * sum_{b > k+C} fz(b)
     // and U(nz-1) * sum_{b < k+C-nz+1} fz(b) on top of the zero-padded k-pass
@@ -596,6 +598,13 @@ __device__ __forceinline__ void adj_sep_body(const Geometry& g, const FusedDims&
     const float* mub = mubar + ((size_t)l * ny) * d.ps + (size_t)i0 * nz;
     float* tsl = slab + ((size_t)v * ny) * d.ps + (size_t)i0 * nz;
 
+    // the first plane's attenuation is requested before anything else
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tma_load_1d(MB, mub + (size_t)j_begin * d.ps, SPECT_MBYTES, bar);
+    }
     // edge-class taps of every plane of the group
     for (int e = tid; e < (j_end - j_begin) * 3 * PT; e += T) {
         const int jj = e / (3 * PT), r3 = e - jj * 3 * PT, c = r3 / PT, a = r3 - c * PT, j = j_begin + jj;
@@ -610,12 +619,6 @@ __device__ __forceinline__ void adj_sep_body(const Geometry& g, const FusedDims&
     // stage the detector plane v(:,:,l) transposed, zero outside the detector
     for (int e = tid; e < d.vrows * d.kpu; e += T) V[e] = 0.f;
     for (int e = tid; e < d.zarea; e += T) Zb[e] = 0.f;
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        mbar_init(bar + 1, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        tma_load_1d(MB, mub + (size_t)j_begin * d.ps, SPECT_MBYTES, bar);
-    }
     __syncthreads();
     for (int e = tid; e < nz * nvr; e += T) {
         const int k = e / nvr, r = e - k * nvr;
