@@ -97,6 +97,34 @@ def test_no_attenuation_map(low_memory):
     assert_close(host(v), v_o, what="A x, mu = 0")
 
 
+@pytest.mark.parametrize("path", ["fused", "lowmem", "rot3"])
+def test_strong_attenuation_over_many_depths(path):
+    """Eq. (1) scanned over 100 depths (three full tiles of 32 and a ragged one)
+    with attenuation up to about exp(-10) across the volume: A, A' and one EM
+    step against the oracle."""
+    from paper_2301_09710_gb300 import SpectPlan
+    nx, nz, nv = 100, 8, 6
+    prob = synthetic.random_problem(11, nx=nx, nz=nz, nview=nv, px=7, pz=5, mu_scale=0.2)
+    ang = oracle.default_angles(nv)
+    rot = "3pass" if path == "rot3" else "bilinear"
+    plan = SpectPlan(nx, nz, nv, mu=prob.mu, dy=prob.dy, fx=prob.fx, fz=prob.fz, angles=ang,
+                     low_memory=(path == "lowmem"), rotation=rot)
+    psf = oracle.psf_from_factors(prob.fx, prob.fz)
+    v = host(plan.forward(dev(prob.x)))
+    assert_close(v, oracle.forward(prob.x, prob.mu, psf, prob.dy, ang, rotation=rot), what="A x, strong attenuation")
+    rng = np.random.default_rng(12)
+    y = rng.uniform(0.5, 2.0, v.shape)
+    assert_close(host(plan.back(dev(y))), oracle.back(y, prob.mu, psf, prob.dy, ang, rotation=rot),
+                 what="A' y, strong attenuation")
+    x0 = np.full(prob.x.shape, 0.5, np.float32)
+    xg = dev(x0)
+    plan.em_step(xg, dev(y), None, niter=1)
+    assert_close(host(xg), oracle.em_step(x0, y, None, prob.mu, psf, prob.dy, ang, rotation=rot),
+                 what="EM step, strong attenuation")
+    plan.check()
+    plan.close()
+
+
 @pytest.mark.parametrize("low_memory", [False, True])
 def test_quarter_turns_exact_line_sums(low_memory):
     # mu = 0, delta PSF, views at multiples of 90 degrees: rotated line sums
