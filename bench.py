@@ -132,7 +132,8 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- workload
-def make_workload(device, path, nview=NVIEW, autotune=True, rotation="bilinear", low_memory=False):
+def make_workload(device, path, nview=NVIEW, autotune=True, rotation="bilinear", low_memory=False,
+                  recompute=False):
     import torch
 
     from paper_2301_09710_gb300 import SpectPlan, synthetic
@@ -141,7 +142,7 @@ def make_workload(device, path, nview=NVIEW, autotune=True, rotation="bilinear",
     sep = path == "separable"
     if sep:
         plan = SpectPlan(NX, NZ, nview, mu=prob.mu, dy=prob.dy, fx=prob.fx, fz=prob.fz, device=device,
-                         rotation=rotation, low_memory=low_memory)
+                         rotation=rotation, low_memory=low_memory, recompute_attenuation=recompute)
         if autotune and not low_memory:
             plan.autotune()  # the library's launch-shape autotuner (timed on this device, outside the timed region)
     else:
@@ -386,6 +387,16 @@ def run_ours(args):
                           "the attenuation of Eq. (1) recomputed from the rotated mu-map in every projection "
                           "(the main line caches it for every view at plan time: plan_bytes there)"}
         lplan.close()
+        # the fused kernels with the attenuation recomputed per view chunk (autotuned)
+        _, cplan, _, _, _ = make_workload(device, "separable", args.nview, recompute=True)
+        cms = side_ms(cplan, args.lowmem_steps)
+        lowmem["recompute_attenuation"] = {
+            "value": 1e3 / cms, "unit": UNIT, "ms_per_step": cms, "plan_bytes": cplan.info()["device_bytes"],
+            "view_chunk": cplan.info()["view_chunk"], "launch_shape": cplan.tuning,
+            "note": "same workload on a SPECT_PLAN_RECOMPUTE_ATTENUATION plan: the fused kernels, the Eq. (1) "
+                    "factors recomputed for each chunk of views before its rotation and its blur adjoint "
+                    "(results bitwise those of the caching main line)"}
+        cplan.close()
     if args.direct_steps > 0 and args.path == "separable":
         _, dplan, _, _, _ = make_workload(device, "direct")
         dms = side_ms(dplan, args.direct_steps)

@@ -95,7 +95,19 @@ enum {
      * The three passes run as one eight-tap gather per output inside the
      * rotation kernel (table: nview*ny*16nx floats) and as eight-entry
      * adjacency lists in A'. */
-    SPECT_PLAN_ROTATION_3PASS = 1u << 2
+    SPECT_PLAN_ROTATION_3PASS = 1u << 2,
+    /* Fused kernels with the attenuation of Eq. (1) recomputed in every
+     * projection instead of cached for every view: the views go through the
+     * fused kernels in chunks, and before each chunk's rotation (A) or blur
+     * adjoint (A') the factors of that chunk's views are computed from the
+     * rotated mu-map (the same warp-scan kernel that fills the cache, so A,
+     * A' and the EM update are bitwise those of a caching plan).  Device
+     * memory then grows with the chunk (work slab and factors of the chunk's
+     * views, 512 MiB by default) rather than with nview * nx*ny*nz.  Bilinear
+     * rotation on the fused kernels only: with SPECT_PLAN_LOW_MEMORY or
+     * SPECT_PLAN_ROTATION_3PASS, or when the fused kernels do not fit the
+     * geometry, spect_plan_create returns SPECT_EUNSUPPORTED. */
+    SPECT_PLAN_RECOMPUTE_ATTENUATION = 1u << 3
 };
 
 /*

@@ -22,6 +22,7 @@ STATUS = {0: "SPECT_OK", 1: "SPECT_EINVAL", 2: "SPECT_ENOMEM", 3: "SPECT_ECUDA",
 SPECT_PLAN_PREFER_SEPARABLE = 1
 SPECT_PLAN_LOW_MEMORY = 2
 SPECT_PLAN_ROTATION_3PASS = 4
+SPECT_PLAN_RECOMPUTE_ATTENUATION = 8
 ROTATIONS = ("bilinear", "3pass")
 KERNEL_CLASSES = ["rotate_atten", "conv_fwd", "conv_adj", "rotate_adj", "other"]
 

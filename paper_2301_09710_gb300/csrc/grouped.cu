@@ -299,7 +299,7 @@ cudaError_t transpose_launches(const std::vector<spect_plan_s*>& plans, float* c
 
 bool groupable(const spect_plan_s& P)
 {
-    return P.fast && P.separable && !P.rot3 && P.gather && P.bucket > 0 && P.chunk >= P.g.nview &&
+    return P.fast && P.separable && !P.rot3 && !P.recompute && P.gather && P.bucket > 0 && P.chunk >= P.g.nview &&
            P.adj_chunk >= P.g.nview;
 }
 

@@ -135,7 +135,7 @@ void free_plan(spect_plan_s* P, cudaStream_t st)
     for (cudaEvent_t e : P->evpool) cudaEventDestroy(e);
     void* ptrs[] = {P->mu, P->psf, P->psf_adj, P->fx, P->fz, P->fx_adj, P->fz_adj, P->rot, P->adj_off, P->adj,
                     P->slab, P->e, P->ratio, P->s, P->mubar, P->xt, P->et, P->st, P->part, P->adjf, P->err, P->rtab, P->ut,
-                    P->gboxes, P->gent, P->rboxes, P->r3_tab};
+                    P->gboxes, P->gent, P->rboxes, P->r3_tab, P->mut};
     for (void* p : ptrs) raw_free(P, p, st);
     delete P;
 }
@@ -152,6 +152,25 @@ size_t slab_budget_bytes(bool fast)
     long mb = env ? atol(env) : (fast ? 1024 : 256);
     if (mb < 1) mb = 1;
     return (size_t)mb << 20;
+}
+
+// Budget of a recomputing plan's per-chunk buffers (work slab plus the
+// attenuation factors of the chunk's views): 512 MiB, or SPECT_SLAB_MB (tuning).
+size_t recompute_budget_bytes()
+{
+    const char* env = getenv("SPECT_SLAB_MB");
+    long mb = env ? atol(env) : 512;
+    if (mb < 1) mb = 1;
+    return (size_t)mb << 20;
+}
+
+// Bytes one view of a chunk takes: its work-slab share, plus its attenuation
+// factors when the plan recomputes them per chunk.
+size_t view_bytes(const spect_plan_s& P, size_t slab_floats_per_view)
+{
+    size_t f = slab_floats_per_view;
+    if (P.recompute) f += (size_t)P.g.ny * P.ps;
+    return f * sizeof(float);
 }
 
 cudaEvent_t pool_event(spect_plan_s* P)
@@ -254,6 +273,9 @@ spect_status fast_forward(spect_plan_s* P, const float* xt, float* v, const floa
     const int nview = P->g.nview;
     for (int l0 = 0; l0 < nview; l0 += P->chunk) {
         const int nv = std::min(P->chunk, nview - l0);
+        if (P->recompute)  // Eq. (1) factors of this chunk's views
+            SPECT_CUDA_TRY(counted(P, SPECT_K_ROTATE_ATTEN, st, [&] { return spect::launch_mubar_range(*P, l0, nv, st); }),
+                           "attenuation launch");
         SPECT_CUDA_TRY(counted(P, SPECT_K_ROTATE_ATTEN, st,
                                [&] { return spect::launch_fused_rotate(*P, xt, l0, nv, st); }),
                        "rotation launch");
@@ -273,6 +295,9 @@ spect_status fast_back(spect_plan_s* P, const float* v, float* out_t, spect::EmA
     for (int l0 = 0; l0 < nview; l0 += P->adj_chunk) {
         const int nv = std::min(P->adj_chunk, nview - l0);
         const bool last = l0 + nv >= nview;
+        if (P->recompute)  // Eq. (1) factors of this chunk's views
+            SPECT_CUDA_TRY(counted(P, SPECT_K_CONV_ADJ, st, [&] { return spect::launch_mubar_range(*P, l0, nv, st); }),
+                           "attenuation launch");
         SPECT_CUDA_TRY(counted(P, SPECT_K_CONV_ADJ, st, [&] { return spect::launch_fused_adjoint(*P, v, l0, nv, st); }),
                        "fused adjoint launch");
         spect::EmArgs e = em;
@@ -350,12 +375,14 @@ size_t plan_bytes_bound(const spect_plan_s& P)
     const size_t csr = (nlist + 1) * sizeof(int) + 4 * nlist * sizeof(spect::AdjEntry);
     b += P.fast ? std::max(fixed, csr) : csr;
     const size_t per_view = std::max(vol, P.fast ? spect::fused_slab_per_view(P) : vol);
-    const size_t chunk = std::max<size_t>(1, std::min<size_t>((size_t)g.nview,
-                                                               slab_budget_bytes(P.fast) / (per_view * F)));
+    const size_t budget = P.recompute ? recompute_budget_bytes() : slab_budget_bytes(P.fast);
+    const size_t chunk = std::max<size_t>(1, std::min<size_t>((size_t)g.nview, budget / view_bytes(P, per_view)));
     b += per_view * chunk * F;
     b += (2 * vol + nproj) * F;
     if (P.fast) {
-        b += (size_t)g.ny * P.ps * g.nview * F + 4 * vol * F;
+        // attenuation factors of every view, or of one chunk plus mu in the internal layout
+        b += P.recompute ? ((size_t)g.ny * P.ps * chunk + vol) * F : (size_t)g.ny * P.ps * g.nview * F;
+        b += 4 * vol * F;
         b += nproj * (size_t)spect::fused_groups(P) * F + (size_t)g.nview * g.ny * P.ts * F;
         // patch gather: boxes and box-local entries (at most 8 per list)
         const size_t np = (size_t)((g.nx + 7) / 8) * ((g.ny + 7) / 8) * g.nview;
@@ -402,6 +429,7 @@ spect_status spect_plan_bytes(int nx, int ny, int nz, int nview, int px, int pz,
         P.fast = P.bucket > 0;
         P.fused_nT = 1;
     }
+    P.recompute = (flags & SPECT_PLAN_RECOMPUTE_ATTENUATION) != 0 && P.fast && !P.rot3;
     *bytes = plan_bytes_bound(P);
     return SPECT_OK;
 }
@@ -422,7 +450,8 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
     if (!(dy >= 0.f) || !isfinite(dy)) return fail(SPECT_EINVAL, "dy must be finite and >= 0");
     if ((psf_fx == nullptr) != (psf_fz == nullptr)) return fail(SPECT_EINVAL, "give both psf_fx and psf_fz or neither");
     if (!psf && !psf_fx) return fail(SPECT_EINVAL, "no PSF given (psf or psf_fx/psf_fz)");
-    if ((flags & ~(unsigned)(SPECT_PLAN_PREFER_SEPARABLE | SPECT_PLAN_LOW_MEMORY | SPECT_PLAN_ROTATION_3PASS)) != 0)
+    if ((flags & ~(unsigned)(SPECT_PLAN_PREFER_SEPARABLE | SPECT_PLAN_LOW_MEMORY | SPECT_PLAN_ROTATION_3PASS |
+                             SPECT_PLAN_RECOMPUTE_ATTENUATION)) != 0)
         return fail(SPECT_EINVAL, "unknown flag bits");
     const void* ins[] = {mu, psf, psf_fx, psf_fz};
     for (const void* p : ins)
@@ -490,6 +519,13 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
     if (P->rot3 && !P->fast) {
         free_plan(P);
         return fail(SPECT_EUNSUPPORTED, "the three-pass rotation runs on the fused kernels (not a low-memory plan)");
+    }
+    P->recompute = (flags & SPECT_PLAN_RECOMPUTE_ATTENUATION) != 0;
+    if (P->recompute && (!P->fast || P->rot3)) {
+        free_plan(P);
+        return fail(SPECT_EUNSUPPORTED,
+                    "recomputed attenuation runs on the fused kernels with the bilinear rotation (not with a "
+                    "low-memory plan, the three-pass rotation, or a geometry the fused kernels do not fit)");
     }
     if (P->separable) {
         P->sep_tk = spect::choose_sep_tile(g, P->cls_z, (size_t)smem_optin);
@@ -592,10 +628,10 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
     }
 
     // work slab and EM buffers
-    const size_t budget = slab_budget_bytes(P->fast);
+    const size_t budget = P->recompute ? recompute_budget_bytes() : slab_budget_bytes(P->fast);
     // the fused path stores padded planes (rotated image planes or adjoint planes)
     const size_t per_view = std::max(vol, P->fast ? spect::fused_slab_per_view(*P) : vol);
-    P->chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)nview, budget / (per_view * sizeof(float))));
+    P->chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)nview, budget / (view_bytes(*P, per_view))));
     PLAN_ALLOC(P->slab, per_view * (size_t)P->chunk, "work slab");
     P->slab_cap = per_view * (size_t)P->chunk;
     // fused adjoint: all views of the slab in one pass by default (measured
@@ -617,9 +653,12 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
     PLAN_ALLOC(P->ratio, nproj, "EM ratio");
     PLAN_ALLOC(P->s, vol, "sensitivity");
 
-    // fused path: attenuation cache for every view, internal-layout buffers
+    // fused path: attenuation cache for every view (or for one view chunk,
+    // recomputed per chunk), internal-layout buffers
     if (P->fast) {
-        PLAN_ALLOC(P->mubar, (size_t)ny * P->ps * nview, "attenuation cache");
+        const int mu_views = P->recompute ? P->chunk : nview;
+        PLAN_ALLOC(P->mubar, (size_t)ny * P->ps * mu_views, "attenuation cache");
+        P->mubar_cap = (size_t)ny * P->ps * mu_views;
         PLAN_ALLOC(P->xt, vol, "internal image");
         PLAN_ALLOC(P->et, vol, "internal back-projection");
         PLAN_ALLOC(P->st, vol, "internal sensitivity");
@@ -639,10 +678,18 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
             raw_free(P, scratch, st);
             PLAN_TRY(e3, "three-pass rotation set-up");
             PLAN_TRY(spect::build_gather(*P, st), "patch gather set-up");  // boxes of the three-pass lists
-        } else {
-            PLAN_TRY(spect::launch_mubar_cache(*P, P->slab, st), "attenuation cache launch");
+        } else if (P->recompute) {
+            // mu stays in the [j][i][k] layout; the factors are made per view chunk
+            PLAN_ALLOC(P->mut, vol, "attenuation map (internal layout)");
+            PLAN_TRY(cudaMemcpyAsync(P->mut, P->slab, vol * sizeof(float), cudaMemcpyDeviceToDevice, st),
+                     "attenuation map copy");
             PLAN_ALLOC(P->rtab, (size_t)nview * ny * P->ts, "rotation tables");
             PLAN_TRY(spect::launch_rot_tables(*P, st), "rotation table launch");
+            PLAN_TRY(spect::build_gather(*P, st), "patch gather set-up");
+        } else {
+            PLAN_ALLOC(P->rtab, (size_t)nview * ny * P->ts, "rotation tables");
+            PLAN_TRY(spect::launch_rot_tables(*P, st), "rotation table launch");
+            PLAN_TRY(spect::launch_mubar_cache(*P, P->slab, st), "attenuation cache launch");
             PLAN_TRY(spect::build_gather(*P, st), "patch gather set-up");
             PLAN_TRY(spect::build_rotpatch(*P, st), "patch rotation set-up");
         }
@@ -945,12 +992,14 @@ spect_status reconfigure(spect_plan_s* P, int J, int adj_J, int tiles, cudaStrea
     P->fused_nT = nt;
     const size_t vol = (size_t)g.nx * g.ny * g.nz, nproj = (size_t)g.nx * g.nz * g.nview;
     const size_t per_view = std::max(vol, spect::fused_slab_per_view(*P));
-    const int chunk = (int)std::max<size_t>(
-        1, std::min<size_t>((size_t)g.nview, slab_budget_bytes(true) / (per_view * sizeof(float))));
+    const size_t budget = P->recompute ? recompute_budget_bytes() : slab_budget_bytes(true);
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)g.nview, budget / view_bytes(*P, per_view)));
     spect_status r = realloc_floats(P, &P->slab, &P->slab_cap, per_view * (size_t)chunk, st, "work slab");
     if (r == SPECT_OK)
         r = realloc_floats(P, &P->part, &P->part_cap, nproj * (size_t)spect::fused_groups(*P), st,
                            "depth-group partial sums");
+    if (r == SPECT_OK && P->recompute)  // the attenuation factors of one chunk
+        r = realloc_floats(P, &P->mubar, &P->mubar_cap, (size_t)g.ny * P->ps * chunk, st, "attenuation factors");
     if (r != SPECT_OK) {
         P->fused_J = oJ;
         P->adj_J = oaJ;
@@ -966,7 +1015,7 @@ spect_status reconfigure(spect_plan_s* P, int J, int adj_J, int tiles, cudaStrea
 // slab (stream-ordered on st) so it holds every view of a fused separable plan.
 spect_status single_pass(spect_plan_s* P, cudaStream_t st)
 {
-    if (!P->fast || !P->separable || P->rot3) return SPECT_OK;
+    if (!P->fast || !P->separable || P->rot3 || P->recompute) return SPECT_OK;
     const Geometry& g = P->g;
     if (P->chunk >= g.nview && P->adj_chunk >= g.nview) return SPECT_OK;
     if (P->adj_chunk_req > 0 && P->adj_chunk_req < g.nview) return SPECT_OK;  // adjoint passes asked for
@@ -1010,7 +1059,7 @@ struct Tuned {
     int J, adj_J, tiles, rotpatch;
 };
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int, int, int>, Tuned> g_tuned;  // per geometry and device
+std::map<std::tuple<int, int, int, int, int, int, int, int>, Tuned> g_tuned;  // per geometry, mode and device
 
 }  // namespace
 
@@ -1039,7 +1088,7 @@ spect_status spect_plan_autotune(spect_plan P, spect_stream stream)
     const Geometry& g = P->g;
     int dev = 0;
     cudaGetDevice(&dev);
-    const auto key = std::make_tuple(dev, g.nx, g.nz, g.nview, g.nvp, P->bucket, (int)P->g.has_mu);
+    const auto key = std::make_tuple(dev, g.nx, g.nz, g.nview, g.nvp, P->bucket, (int)P->g.has_mu, P->recompute);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(key);

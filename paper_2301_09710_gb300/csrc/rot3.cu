@@ -125,37 +125,20 @@ __global__ void __launch_bounds__(256) k_gather_taps(Geometry g, int tsn, const 
 }
 
 // mubar[l][j][i][k] from the rotated map mu~ of view l ([j][i][k], dense):
-// Eq. (1) from the detector side, as k_mubar_cache does for the bilinear
-// rotation -- one block per 32 consecutive (i, k) columns, tiles of 32 depths
-// loaded and stored with lanes over the columns, scanned along depth by warps
-// (atten_warp_scan).
-__global__ void __launch_bounds__(256) k_mubar_rotated(Geometry g, int ps, const float* __restrict__ mu_rot, int l,
-                                                       float* __restrict__ mubar)
+// Eq. (1) walked from the detector side with a compensated running sum, one
+// thread per (i, k) column (coalesced), the same arithmetic as the bilinear
+// rotation's attenuation cache (k_mubar_cache).
+__global__ void k_mubar_rotated(Geometry g, int ps, const float* __restrict__ mu_rot, int l,
+                                float* __restrict__ mubar)
 {
-    __shared__ float tile[32][33];
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     const int per = g.nx * g.nz;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int idx = blockIdx.x * 32 + lane;
+    if (idx >= per) return;
     const size_t pln = (size_t)per;
-    DFloat carry[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    for (int j0 = g.ny - 1; j0 >= 0; j0 -= 32) {
-        for (int q = warp; q < 32; q += 8) {
-            const int j = j0 - q;
-            tile[q][lane] = (j >= 0 && idx < per) ? mu_rot[(size_t)j * pln + idx] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int c = warp + 8 * t;
-            const float m = tile[lane][c];
-            tile[lane][c] = g.has_mu ? atten_warp_scan(m, carry[t], g.dy) : 1.f;
-        }
-        __syncthreads();
-        for (int q = warp; q < 32; q += 8) {
-            const int j = j0 - q;
-            if (j >= 0 && idx < per) mubar[((size_t)l * g.ny + j) * ps + idx] = tile[q][lane];
-        }
-        __syncthreads();
+    AttenScan sc;
+    for (int j = g.ny - 1; j >= 0; --j) {
+        const float m = mu_rot[(size_t)j * pln + idx];
+        mubar[((size_t)l * g.ny + j) * ps + idx] = g.has_mu ? sc.step(m, g.dy) : 1.f;
     }
 }
 
@@ -250,7 +233,7 @@ cudaError_t build_rot3(spect_plan_s& P, const double* angles, const float* mu_t,
     // the attenuation cache from mu turned by the same taps, view by view
     for (int l = 0; l < nview && e == cudaSuccess; ++l) {
         k_gather_taps<8><<<n, 256, 0, st>>>(g, ts8, P.r3_tab, mu_t, scratch, l);
-        k_mubar_rotated<<<(unsigned)((pln + 31) / 32), 256, 0, st>>>(g, ps, scratch, l, P.mubar);
+        k_mubar_rotated<<<(unsigned)((pln + 255) / 256), 256, 0, st>>>(g, ps, scratch, l, P.mubar);
         e = cudaGetLastError();
     }
     // the host vectors must outlive the asynchronous uploads

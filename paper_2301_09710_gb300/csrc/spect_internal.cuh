@@ -104,6 +104,12 @@ struct spect_plan_s {
     // used instead of k_rot_fwd when rotpatch_on != 0 (chosen by the autotuner)
     int rotpatch = 0;
     int rotpatch_on = 0;
+    // SPECT_PLAN_RECOMPUTE_ATTENUATION: mubar holds the factors of one view
+    // chunk (views l0 .. l0+chunk-1 at chunk-relative positions), recomputed
+    // from mut (mu in the [j][i][k] layout) before each chunk's kernels
+    int recompute = 0;
+    float* mut = nullptr;
+    size_t mubar_cap = 0;        // floats allocated for mubar
     // three-pass rotation (rot3.cu): the eight-tap table of the forward
     // rotation, [l][j] blocks of rot3_ts8(nx) floats (the adjoint's lists
     // are in adjf)
@@ -421,6 +427,17 @@ cudaError_t launch_fwd_reduce(const spect_plan_s& P, float* v, const float* em_y
 cudaError_t build_gather(spect_plan_s& P, cudaStream_t st);
 cudaError_t build_rotpatch(spect_plan_s& P, cudaStream_t st);
 cudaError_t launch_rot_patch(const spect_plan_s& P, int l0, int nv, cudaStream_t st);
+// the attenuation factors of views l0 .. l0+nv-1 (recomputing plans: into the chunk buffer)
+cudaError_t launch_mubar_range(const spect_plan_s& P, int l0, int nv, cudaStream_t st);
+// The attenuation array as the kernels index it, mubar + (l ny + j) ps for view l:
+// a recomputing plan holds views l0.. at chunk-relative positions, so its base is
+// moved back by l0 views (computed on integers; every access lands in the buffer).
+inline const float* mubar_for(const spect_plan_s& P, int l0)
+{
+    if (!P.recompute) return P.mubar;
+    return reinterpret_cast<const float*>(reinterpret_cast<uintptr_t>(P.mubar) -
+                                          (uintptr_t)l0 * P.g.ny * P.ps * sizeof(float));
+}
 cudaError_t launch_adj_gather(const spect_plan_s& P, int l0, int nv, float* out, int accumulate, EmArgs em,
                               cudaStream_t st);
 cudaError_t launch_adj_rot_t(const spect_plan_s& P, int l0, int nv, float* out, int accumulate, EmArgs em,

@@ -124,11 +124,12 @@ def _rotation_flag(rotation: str) -> int:
 
 
 def plan_bytes(nx: int, nz: int, nview: int, px: int, pz: int, nview_psf: int = 1, separable: bool = True,
-               low_memory: bool = False, rotation: str = "bilinear") -> int:
+               low_memory: bool = False, rotation: str = "bilinear", recompute_attenuation: bool = False) -> int:
     """Upper bound of the device bytes a plan of this geometry allocates (no allocation)."""
     lib = _lib.load()
     out = ctypes.c_size_t()
-    flags = (_lib.SPECT_PLAN_LOW_MEMORY if low_memory else 0) | _rotation_flag(rotation)
+    flags = (_lib.SPECT_PLAN_LOW_MEMORY if low_memory else 0) | _rotation_flag(rotation) | \
+        (_lib.SPECT_PLAN_RECOMPUTE_ATTENUATION if recompute_attenuation else 0)
     _lib.check(lib.spect_plan_bytes(int(nx), int(nx), int(nz), int(nview), int(px), int(pz), int(nview_psf),
                                     int(bool(separable)), flags, ctypes.byref(out)))
     return out.value
@@ -139,11 +140,14 @@ class SpectPlan:
 
     rotation: "bilinear" (default) or "3pass", the two image rotations of
     Section II-A (the three-pass one on the fused kernels only).
+    recompute_attenuation: the fused kernels with the Eq. (1) factors made per
+    view chunk instead of cached for every view (bitwise the same results,
+    memory bounded by the chunk; SPECT_PLAN_RECOMPUTE_ATTENUATION).
     """
 
     def __init__(self, nx: int, nz: int, nview: int, mu=None, dy: float = 1.0, psf=None, fx=None, fz=None,
                  angles=None, prefer_separable: bool = True, low_memory: bool = False, device=None, stream=None,
-                 rotation: str = "bilinear"):
+                 rotation: str = "bilinear", recompute_attenuation: bool = False):
         self.lib = _lib.load()
         self.device = torch.device(device if device is not None else "cuda")
         self.nx = self.ny = int(nx)
@@ -164,7 +168,8 @@ class SpectPlan:
             ang = self._angles.ctypes.data_as(ctypes.c_void_p)
         handle = ctypes.c_void_p()
         flags = (_lib.SPECT_PLAN_PREFER_SEPARABLE if prefer_separable else 0) | \
-            (_lib.SPECT_PLAN_LOW_MEMORY if low_memory else 0) | _rotation_flag(rotation)
+            (_lib.SPECT_PLAN_LOW_MEMORY if low_memory else 0) | _rotation_flag(rotation) | \
+            (_lib.SPECT_PLAN_RECOMPUTE_ATTENUATION if recompute_attenuation else 0)
         self.rotation = rotation
         with torch.cuda.device(self.device):
             _lib.check(self.lib.spect_plan_create(
