@@ -23,6 +23,8 @@
 //    into blurred-adjoint planes times mubar (the t slab, [v][j][i][k]); a
 //    gather kernel then sums sum_l sum_p W_l(p;q) t_l(p,k) per destination voxel
 //    q over fixed-length adjacency lists (weights bitwise those of A).
+#include <algorithm>
+
 #include "fused_body.cuh"
 
 namespace spect {
@@ -46,15 +48,17 @@ cudaError_t launch_transpose(const float* in, float* out, int R, int C, cudaStre
 }
 
 // mubar[l][j][i][k] = exp(-dy (mu~(j)/2 + sum_{s>j} mu~(s))), Eq. (1), for every
-// view.  One thread per column (i, k) of view l = l0 + v walks depth from the
-// detector side with a compensated running sum (AttenScan); lanes run over k,
-// so the four corner loads of each depth and the stores are coalesced, and
-// the bilinear weights and base voxel come from the plan's rotation tables
-// (the forward rotation's own).  With nview * nx * nz independent columns
-// this does O(1) work per factor; a warp scan along depth
-// (atten_warp_scan) would do O(log 32) and measured 2.6x slower here.  mu_t is
-// mu in the [j][i][k] layout; planes (l, j) are ps floats apart (16-byte
-// aligned for bulk copies); view l is written at position v.
+// view.  One block per (row i, view l = l0 + v, run of up to kMuThreads columns k):
+// the block first stages the rotation-table entries of row i for every depth
+// (the forward rotation's bilinear weights and base voxels) in shared memory,
+// then each thread walks one column k from the detector side with a
+// compensated running sum (AttenScan).  Lanes run over k, so the corner loads
+// and the stores are coalesced, and a depth step's loads depend on nothing
+// but the staged table, so the unrolled walk keeps several steps in flight.
+// With nview * nx * nz independent columns this does O(1) work per factor; a
+// warp scan along depth (atten_warp_scan) would do O(log 32) and measured
+// 2.6x slower here.  mu_t is mu in the [j][i][k] layout; planes (l, j) are ps
+// floats apart (16-byte aligned for bulk copies); view l lands at position v.
 constexpr int kMuThreads = 128;
 
 __global__ void __launch_bounds__(kMuThreads) k_mubar_cache(Geometry g, int ps, int ts,
@@ -62,24 +66,29 @@ __global__ void __launch_bounds__(kMuThreads) k_mubar_cache(Geometry g, int ps, 
                                                             const float* __restrict__ mu_t,
                                                             float* __restrict__ mubar, int l0)
 {
-    const int idx = blockIdx.x * kMuThreads + threadIdx.x, v = blockIdx.y, l = l0 + v;
-    const int per = g.nx * g.nz;
-    if (idx >= per) return;
-    const int i = idx / g.nz, k = idx - i * g.nz;
-    const size_t rs = (size_t)g.nx * g.nz;
+    extern __shared__ __align__(16) float smu[];
+    float4* TW = reinterpret_cast<float4*>(smu);        // [ny] weights of row i
+    int* TB = reinterpret_cast<int*>(smu + 4 * g.ny);   // [ny] base voxels of row i
+    const int k = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y, v = blockIdx.z, l = l0 + v;
     const float* tab_l = rtab + (size_t)l * g.ny * ts;
-    float* out = mubar + (size_t)v * g.ny * ps + idx;
+    for (int j = threadIdx.x; j < g.ny; j += blockDim.x) {
+        const float* tab = tab_l + (size_t)j * ts;
+        TW[j] = __ldg(reinterpret_cast<const float4*>(tab) + i);
+        TB[j] = __ldg(reinterpret_cast<const int*>(tab + 4 * g.nx) + i);
+    }
+    __syncthreads();
+    if (k >= g.nz) return;
+    const size_t rs = (size_t)g.nx * g.nz;
+    float* out = mubar + (size_t)v * g.ny * ps + (size_t)i * g.nz + k;
     if (!g.has_mu) {
         for (int j = 0; j < g.ny; ++j) out[(size_t)j * ps] = 1.f;
         return;
     }
     AttenScan sc;
-#pragma unroll 4
+#pragma unroll 8
     for (int j = g.ny - 1; j >= 0; --j) {
-        const float* tab = tab_l + (size_t)j * ts;
-        const float4 w = __ldg(reinterpret_cast<const float4*>(tab) + i);
-        const int base = __ldg(reinterpret_cast<const int*>(tab + 4 * g.nx) + i);
-        const float* m = mu_t + (size_t)base * g.nz + k;
+        const float4 w = TW[j];
+        const float* m = mu_t + (size_t)TB[j] * g.nz + k;
         float mv = 0.f;
         mv = __fmaf_rn(w.x, __ldg(m), mv);
         mv = __fmaf_rn(w.y, __ldg(m + g.nz), mv);
@@ -89,19 +98,31 @@ __global__ void __launch_bounds__(kMuThreads) k_mubar_cache(Geometry g, int ps, 
     }
 }
 
+namespace {
+cudaError_t mubar_launch(const spect_plan_s& P, const float* mu_t, int l0, int nv, cudaStream_t st)
+{
+    const size_t smem = (size_t)P.g.ny * 5 * sizeof(float);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_mubar_cache, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    // a run of columns k per block: nz rounded up to whole warps, at most kMuThreads
+    const int thr = std::min(kMuThreads, (P.g.nz + 31) & ~31);
+    const dim3 grid((P.g.nz + thr - 1) / thr, P.g.nx, nv);
+    k_mubar_cache<<<grid, thr, smem, st>>>(P.g, P.ps, P.ts, P.rtab, mu_t, P.mubar, l0);
+    return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t launch_mubar_cache(const spect_plan_s& P, const float* mu_t, cudaStream_t st)
 {
-    const dim3 grid((P.g.nx * P.g.nz + kMuThreads - 1) / kMuThreads, P.g.nview);
-    k_mubar_cache<<<grid, kMuThreads, 0, st>>>(P.g, P.ps, P.ts, P.rtab, mu_t, P.mubar, 0);
-    return cudaGetLastError();
+    return mubar_launch(P, mu_t, 0, P.g.nview, st);
 }
 
 cudaError_t launch_mubar_range(const spect_plan_s& P, int l0, int nv, cudaStream_t st)
 {
     if (!P.recompute || !P.mut || nv < 1 || (size_t)nv * P.g.ny * P.ps > P.mubar_cap) return cudaErrorInvalidValue;
-    const dim3 grid((P.g.nx * P.g.nz + kMuThreads - 1) / kMuThreads, nv);
-    k_mubar_cache<<<grid, kMuThreads, 0, st>>>(P.g, P.ps, P.ts, P.rtab, P.mut, P.mubar, l0);
-    return cudaGetLastError();
+    return mubar_launch(P, P.mut, l0, nv, st);
 }
 
 // Rotation tables of every (view, depth row), the per-plane input of the fused
