@@ -173,6 +173,17 @@ size_t view_bytes(const spect_plan_s& P, size_t slab_floats_per_view)
     return f * sizeof(float);
 }
 
+// The patch gather reads its own box-local copy of the adjacency entries, so
+// once it is set up the fixed-length lists were set-up input only: free them.
+void drop_fixed_lists(spect_plan_s* P, cudaStream_t st)
+{
+    if (!P->gather || !P->adjf) return;
+    const size_t nlist = (size_t)P->g.nx * P->g.ny * P->g.nview;
+    raw_free(P, P->adjf, st);
+    P->adjf = nullptr;
+    P->bytes -= nlist * (size_t)std::max(P->adj_max, 1) * sizeof(spect::AdjEntry);
+}
+
 cudaEvent_t pool_event(spect_plan_s* P)
 {
     if (!P->evpool.empty()) {
@@ -678,6 +689,7 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
             raw_free(P, scratch, st);
             PLAN_TRY(e3, "three-pass rotation set-up");
             PLAN_TRY(spect::build_gather(*P, st), "patch gather set-up");  // boxes of the three-pass lists
+            drop_fixed_lists(P, st);
         } else if (P->recompute) {
             // mu stays in the [j][i][k] layout; the factors are made per view chunk
             PLAN_ALLOC(P->mut, vol, "attenuation map (internal layout)");
@@ -686,11 +698,13 @@ spect_status spect_plan_create(spect_plan* out, int nx, int ny, int nz, int nvie
             PLAN_ALLOC(P->rtab, (size_t)nview * ny * P->ts, "rotation tables");
             PLAN_TRY(spect::launch_rot_tables(*P, st), "rotation table launch");
             PLAN_TRY(spect::build_gather(*P, st), "patch gather set-up");
+            drop_fixed_lists(P, st);
         } else {
             PLAN_ALLOC(P->rtab, (size_t)nview * ny * P->ts, "rotation tables");
             PLAN_TRY(spect::launch_rot_tables(*P, st), "rotation table launch");
             PLAN_TRY(spect::launch_mubar_cache(*P, P->slab, st), "attenuation cache launch");
             PLAN_TRY(spect::build_gather(*P, st), "patch gather set-up");
+            drop_fixed_lists(P, st);
             PLAN_TRY(spect::build_rotpatch(*P, st), "patch rotation set-up");
         }
     }
