@@ -1125,7 +1125,7 @@ spect_status spect_plan_autotune(spect_plan P, spect_stream stream)
         if (t <= nib && std::find(tile_cands.begin(), tile_cands.end(), t) == tile_cands.end()) tile_cands.push_back(t);
     if (!P->separable) tile_cands.assign(1, 1);  // the full-PSF kernels run untiled
     std::vector<int> Js;
-    for (int J : {4, 8, 16, 24, 32})
+    for (int J : {4, 8, 12, 16, 20, 24, 32})
         if (J <= std::max(g.ny, 4)) Js.push_back(J);
     Tuned best{P->fused_J, P->adj_J, base, 0};
     P->rotpatch_on = 0;
