@@ -345,8 +345,10 @@ spect_status spect_plan_release(spect_plan plan, spect_stream stream);
  * fused_J / adj_J: depth planes per block of the forward / adjoint blur
  * kernels (1..32); tiles: column tiles per plane (>= 1; the kernels use the
  * nearest count that divides the plane into whole 16-column runs).  The plan
- * grows its work slab and partial-sum buffer in stream order on `stream` when
- * the shape needs more room.  Results stay within the FP32 tolerance of the
+ * grows its work slab and partial-sum buffer (and, for a plan made with
+ * SPECT_PLAN_RECOMPUTE_ATTENUATION, its buffer of one view chunk's
+ * attenuation factors) in stream order on `stream` when the shape needs more
+ * room.  Results stay within the FP32 tolerance of the
  * oracle for every shape; A' is bitwise independent of the shape, A x depends
  * on fused_J only through the grouping of its depth sum.
  * Errors: SPECT_EINVAL, SPECT_EUNSUPPORTED (low-memory plan, or the shape
