@@ -106,7 +106,8 @@ def test_autotune_picks_a_valid_shape_and_caches_it():
     psf = oracle_psf(prob, "fused")
     p1 = make_plan(prob, ang, "fused")
     t1 = p1.autotune()
-    assert t1["fused_J"] in (4, 8, 16, 24, 32) and t1["adj_J"] in (4, 8, 16, 24, 32) and t1["tiles"] >= 1
+    assert t1["fused_J"] in (4, 8, 12, 16, 20, 24, 32) and t1["adj_J"] in (4, 8, 12, 16, 20, 24, 32)
+    assert t1["tiles"] >= 1
     p2 = make_plan(prob, ang, "fused")
     assert p2.autotune() == t1     # same geometry: the cached choice
     x = dev(prob.x)
