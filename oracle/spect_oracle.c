@@ -29,7 +29,7 @@
  *      so image content turns by +t.  At exact multiples of pi/2 the
  *      cosine and sine are taken as exact 0/+-1.
  *   R2 bilinear interpolation with zero padding: neighbours outside the
- *      grid contribute 0 (Section II-A, "zero padding boundary condition").
+ *      grid contribute 0 (Section II-A: the rotation pads the image with zeros).
  *   R3 Eq. (1) attenuation: plane j = ny-1 is nearest the detector,
  *      S(j) = mu~(j)/2 + sum_{s>j} mu~(s), mubar = exp(-dy * S).
  *   R4 PSF blur is a true convolution with replicate padding in i and k

@@ -1,4 +1,4 @@
-"""Differentiation through the projector (Section II-A, "customized the chain rule")
+"""Differentiation through the projector (Section II-A: the backward pass of A is A', written by hand)
 and the unrolled CNN-regularised EM of Algorithm 3 (Section II-B).
 
 * ``project(x, plan)`` is A x with backward A' g; ``backproject(v, plan)`` is A' v
