@@ -159,3 +159,32 @@ def test_benchmark_plan_all_views_vs_oracle(prob):
                  what="MLEM step, all 128 views")
     plan.check()
     plan.close()
+
+
+# geometries whose planes do not fit one block's shared memory, so the fused
+# kernels cut them into column tiles on their own (no tiling knob set)
+LARGE = [(192, 128, 4, 37, 0.2), (256, 64, 4, 21, 0.1)]
+
+
+@pytest.mark.parametrize("case", LARGE, ids=[f"{c[0]}x{c[1]}p{c[3]}" for c in LARGE])
+def test_large_naturally_tiled_geometry_vs_oracle(case):
+    from paper_2301_09710_gb300 import SpectPlan
+    nx, nz, nv, p, mu_scale = case
+    prob = synthetic.random_problem(nx + p, nx=nx, nz=nz, nview=nv, px=p, pz=p, mu_scale=mu_scale / nx * 16)
+    ang = oracle.default_angles(nv) + 0.3
+    plan = SpectPlan(nx, nz, nv, mu=prob.mu, dy=prob.dy, fx=prob.fx, fz=prob.fz, angles=ang)
+    assert plan.info()["fused"] and plan.tuning["tiles"] > 1, plan.tuning
+    psf = oracle.psf_from_factors(prob.fx, prob.fz)
+    v = host(plan.forward(dev(prob.x)))
+    assert_close(v, oracle.forward(prob.x, prob.mu, psf, prob.dy, ang), what=f"A x, {nx}x{nx}x{nz}, tiled")
+    rng = np.random.default_rng(nx)
+    y = rng.uniform(0.5, 2.0, v.shape)
+    assert_close(host(plan.back(dev(y))), oracle.back(y, prob.mu, psf, prob.dy, ang),
+                 what=f"A' y, {nx}x{nx}x{nz}, tiled")
+    x0 = np.full(prob.x.shape, 0.5, np.float32)
+    xg = dev(x0)
+    plan.em_step(xg, dev(y), None, niter=1)
+    assert_close(host(xg), oracle.em_step(x0, y, None, prob.mu, psf, prob.dy, ang),
+                 what=f"EM step, {nx}x{nx}x{nz}, tiled")
+    plan.check()
+    plan.close()
