@@ -103,23 +103,25 @@ class GpuExecutor:
         return time.perf_counter() - self.t0
 
     @staticmethod
-    def plan_bytes(req: Request) -> int:
+    def plan_bytes(req: Request, compact: bool = False) -> int:
         """Device memory one request holds while admitted: the library's bound
         on its plan (spect_plan_bytes), plus iterate, data and background, plus
-        slack for allocator rounding."""
+        slack for allocator rounding.  compact: the plan recomputes the
+        attenuation per view chunk (SPECT_PLAN_RECOMPUTE_ATTENUATION) instead
+        of caching it for every view."""
         from .projector import plan_bytes
         nvp, _, px = req.fx.shape
         pz = req.fz.shape[-1]
-        plan = plan_bytes(req.nx, req.nz, req.nview, px, pz, nvp, separable=True)
+        plan = plan_bytes(req.nx, req.nz, req.nview, px, pz, nvp, separable=True, recompute_attenuation=compact)
         tensors = 4 * (req.nx * req.nx * req.nz + 2 * req.nview * req.nz * req.nx)
         return int((plan + tensors) * 1.02) + (8 << 20)
 
-    def _create(self, req: Request, st):
+    def _create(self, req: Request, st, compact: bool = False):
         from .projector import SpectPlan
         torch = self.torch
         with torch.cuda.device(self.device), torch.cuda.stream(st):
             plan = SpectPlan(req.nx, req.nz, req.nview, mu=req.mu, dy=req.dy, fx=req.fx, fz=req.fz,
-                             device=self.device, stream=st)
+                             device=self.device, stream=st, recompute_attenuation=compact)
             x0 = req.x0 if req.x0 is not None else np.ones((req.nz, req.nx, req.nx), np.float32)
             x = torch.from_numpy(np.ascontiguousarray(x0, np.float32)).to(self.device)
             y = torch.from_numpy(np.ascontiguousarray(req.y, np.float32)).to(self.device)
@@ -129,11 +131,11 @@ class GpuExecutor:
         self.plan_bytes_seen.append((req.rid, plan.info()["device_bytes"]))
         return plan, x, y, rb
 
-    def start(self, req: Request, slot: int):
+    def start(self, req: Request, slot: int, compact: bool = False):
         st = self.streams[slot % len(self.streams)]
-        h = {"future": self.pool.submit(self._create, req, st), "plan": None, "stream": st,
+        h = {"future": self.pool.submit(self._create, req, st, compact), "plan": None, "stream": st,
              "left": req.niter, "event": None}
-        self._pending[id(h)] = self.plan_bytes(req)
+        self._pending[id(h)] = self.plan_bytes(req, compact)
         return h
 
     def step(self, h) -> None:
@@ -199,14 +201,15 @@ class FakeExecutor:
         return 0
 
     @staticmethod
-    def plan_bytes(req: Request) -> int:
-        return req.nx * req.nx * req.nz * req.nview
+    def plan_bytes(req: Request, compact: bool = False) -> int:
+        full = req.nx * req.nx * req.nz * req.nview
+        return full // 4 if compact else full  # a compact plan: a quarter of the memory
 
-    def start(self, req, slot):
+    def start(self, req, slot, compact: bool = False):
         self.t += self.plan_cost
-        self.held += self.plan_bytes(req)
-        self.log.append(("start", req.rid, self.t))
-        return {"rid": req.rid, "left": req.niter, "busy_until": self.t, "bytes": self.plan_bytes(req)}
+        self.held += self.plan_bytes(req, compact)
+        self.log.append(("start", req.rid, self.t, compact))
+        return {"rid": req.rid, "left": req.niter, "busy_until": self.t, "bytes": self.plan_bytes(req, compact)}
 
     def step(self, h):
         h["busy_until"] = max(h["busy_until"], self.t) + self.iter_cost
@@ -237,6 +240,7 @@ class ServeStats:
     peak_bytes: int = 0
     peak_active: int = 0
     held_back: int = 0          # admissions deferred because the device's live free memory was short
+    compact: int = 0            # requests admitted with a compact plan (compact_fallback)
     budget: int = 0
 
     def summary(self) -> dict:
@@ -245,14 +249,14 @@ class ServeStats:
                 "p50_s": float(np.percentile(lat, 50)), "p95_s": float(np.percentile(lat, 95)),
                 "p99_s": float(np.percentile(lat, 99)), "makespan_s": self.makespan,
                 "peak_active": self.peak_active, "peak_bytes": self.peak_bytes, "budget_bytes": self.budget,
-                "held_back_by_free_memory": self.held_back}
+                "held_back_by_free_memory": self.held_back, "compact_admissions": self.compact}
 
 
 RESERVE_BYTES = 2 << 30  # device memory the server leaves free for everything else
 
 
 def serve(requests, executor, mem_budget=None, max_active: int = 16, poll_sleep: float = 0.0,
-          reserve_bytes: int = RESERVE_BYTES) -> ServeStats:
+          reserve_bytes: int = RESERVE_BYTES, compact_fallback: bool = False) -> ServeStats:
     """Continuous batching: admit by memory and slots, interleave EM iterations
     round-robin, retire finished requests immediately.
 
@@ -260,7 +264,13 @@ def serve(requests, executor, mem_budget=None, max_active: int = 16, poll_sleep:
     memory at the start less ``reserve_bytes``.  Each admission also needs the
     request's bytes free on the device at that moment (live free memory, less
     the bytes of plans still being built, less the reserve), unless nothing is
-    admitted (memory released in stream order may not show as free yet)."""
+    admitted (memory released in stream order may not show as free yet).
+
+    compact_fallback: a request whose plan does not fit now is admitted with a
+    compact plan (the attenuation recomputed per view chunk, a fraction of the
+    memory, slower iterations) when that fits, instead of waiting.  Its image
+    then matches the caching plan's within the FP32 tolerance rather than bit for
+    bit (its back-projection sums the views in chunks)."""
     free0 = executor.free_bytes() if hasattr(executor, "free_bytes") else None
     if mem_budget is None:
         if free0 is None:
@@ -281,19 +291,30 @@ def serve(requests, executor, mem_budget=None, max_active: int = 16, poll_sleep:
             pi += 1
         # admission in arrival order while memory and slots allow
         while queue and slots_free:
-            need = executor.plan_bytes(queue[0])
-            if need > mem_budget:
-                raise ValueError(f"request {queue[0].rid} needs {need} bytes, more than the whole budget")
-            if used + need > mem_budget:
-                break
-            if active and free0 is not None:
-                live = executor.free_bytes() - executor.pending_bytes() - reserve_bytes
-                if need > live:
+            def short_of(n):  # None if n bytes fit now, else what they are short of
+                if used + n > mem_budget:
+                    return "budget"
+                if active and free0 is not None:
+                    live = executor.free_bytes() - executor.pending_bytes() - reserve_bytes
+                    if n > live:
+                        return "live"
+                return None
+
+            need, compact = executor.plan_bytes(queue[0]), False
+            smallest = min(need, executor.plan_bytes(queue[0], compact=True)) if compact_fallback else need
+            if smallest > mem_budget:
+                raise ValueError(f"request {queue[0].rid} needs {smallest} bytes, more than the whole budget")
+            short = short_of(need)
+            if short and smallest < need and short_of(smallest) is None:
+                need, compact, short = smallest, True, None
+            if short:
+                if short == "live":
                     stats.held_back += 1
-                    break
+                break
             req = queue.pop(0)
             slot = slots_free.pop(0)
-            h = executor.start(req, slot)
+            h = executor.start(req, slot, compact) if compact else executor.start(req, slot)
+            stats.compact += int(compact)
             used += need
             active.append([req, h, executor.now(), slot, need])
             stats.peak_bytes = max(stats.peak_bytes, used)

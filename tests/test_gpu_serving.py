@@ -77,3 +77,28 @@ def test_plan_bytes_bounds_what_a_plan_allocates(shape, low_memory):
     if not low_memory:
         req = Request(0, 0.0, nx, nz, nv, 1, mu, fx, fz, np.zeros((nv, nz, nx), np.float32))
         assert GpuExecutor.plan_bytes(req) >= held + 4 * (nx * nx * nz + 2 * nv * nz * nx)
+
+
+def test_compact_fallback_on_the_gpu(monkeypatch):
+    """A request that does not fit beside a running one is admitted with a
+    compact plan (attenuation recomputed per view chunk) and its image matches
+    the caching plan's within the FP32 tolerance."""
+    monkeypatch.setenv("SPECT_SLAB_MB", "8")  # chunks of a few views, so compact plans are smaller
+    # 64x64x32, 60 views: the attenuation of every view (31 MB) dominates the plan
+    reqs = make_requests(2, rate=2000.0, seed=21, large_frac=0.0, iters=(3, 3), sizes=(64,), nzs=(32,),
+                         views=(60,), psfs=(7,))
+    reqs[0].niter = 24  # the first one runs long
+    full = [GpuExecutor.plan_bytes(q) for q in reqs]
+    small = [GpuExecutor.plan_bytes(q, compact=True) for q in reqs]
+    assert small[1] < full[1]
+    budget = max(full[1], full[0] + small[1])
+    assert full[0] + full[1] > budget
+    ex = GpuExecutor(n_streams=2, iters_per_step=1)
+    st = serve(reqs, ex, mem_budget=budget, max_active=4, compact_fallback=True)
+    ex.close()
+    assert st.compact == 1 and st.peak_active == 2 and st.peak_bytes <= budget
+    ex1 = GpuExecutor(n_streams=1, iters_per_step=3)
+    alone = serve_plain(reqs, ex1)
+    ex1.close()
+    for a, b in zip(st.results, alone.results):
+        assert_close(a.x, b.x, rel_l2=1e-5, max_rel=1e-3, what=f"request {a.rid}: compact vs caching plan")

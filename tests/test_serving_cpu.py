@@ -84,3 +84,32 @@ def test_memory_taken_by_another_tenant_holds_admission_back():
 def test_serving_without_a_budget_needs_a_device_that_reports_free_memory():
     with pytest.raises(ValueError, match="mem_budget"):
         serve([_req(0, 0.0)], FakeExecutor(), mem_budget=None)
+
+
+def test_compact_fallback_admits_what_only_fits_as_a_compact_plan():
+    # the second request's full plan fits alone but not beside the first one,
+    # its compact plan (a quarter on the simulated device) does
+    reqs = [_req(0, 0.0, niter=10), _req(1, 0.001, nx=16), _req(2, 0.002)]
+    small, big = FakeExecutor.plan_bytes(reqs[0]), FakeExecutor.plan_bytes(reqs[1])
+    budget = big + small // 2
+    ex = FakeExecutor(iter_cost=0.01)
+    st = serve(reqs, ex, mem_budget=budget, max_active=4, compact_fallback=True)
+    starts = {e[1]: (e[2], e[3]) for e in ex.log if e[0] == "start"}
+    assert st.compact == 1 and starts[1][1] is True and starts[0][1] is False
+    assert starts[1][0] < 0.05, "the compact request waited for the first one to finish"
+    assert st.peak_bytes <= budget and [r.rid for r in st.results] == [0, 1, 2]
+    # without the fallback the same request waits for the first to finish
+    ex2 = FakeExecutor(iter_cost=0.01)
+    st2 = serve(reqs, ex2, mem_budget=budget, max_active=4)
+    starts2 = {e[1]: e[2] for e in ex2.log if e[0] == "start"}
+    assert st2.compact == 0 and starts2[1] >= 10 * 0.01 - 1e-9
+
+
+def test_compact_fallback_still_refuses_what_no_plan_can_fit():
+    reqs = [_req(0, 0.0, nx=16)]
+    with pytest.raises(ValueError):
+        serve(reqs, FakeExecutor(), mem_budget=FakeExecutor.plan_bytes(reqs[0], compact=True) - 1,
+              compact_fallback=True)
+    st = serve(reqs, FakeExecutor(), mem_budget=FakeExecutor.plan_bytes(reqs[0], compact=True),
+               compact_fallback=True)
+    assert st.compact == 1 and len(st.results) == 1
