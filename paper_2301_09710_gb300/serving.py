@@ -284,6 +284,16 @@ def serve(requests, executor, mem_budget=None, max_active: int = 16, poll_sleep:
     stats = ServeStats()
     stats.budget = int(mem_budget)
     pi = 0
+
+    def short_of(n):  # None if n more bytes fit now, else what they are short of
+        if used + n > mem_budget:
+            return "budget"
+        if active and free0 is not None:
+            live = executor.free_bytes() - executor.pending_bytes() - reserve_bytes
+            if n > live:
+                return "live"
+        return None
+
     while pi < len(pending) or queue or active:
         now = executor.now()
         while pi < len(pending) and pending[pi].arrival <= now:
@@ -291,15 +301,6 @@ def serve(requests, executor, mem_budget=None, max_active: int = 16, poll_sleep:
             pi += 1
         # admission in arrival order while memory and slots allow
         while queue and slots_free:
-            def short_of(n):  # None if n bytes fit now, else what they are short of
-                if used + n > mem_budget:
-                    return "budget"
-                if active and free0 is not None:
-                    live = executor.free_bytes() - executor.pending_bytes() - reserve_bytes
-                    if n > live:
-                        return "live"
-                return None
-
             need, compact = executor.plan_bytes(queue[0]), False
             smallest = min(need, executor.plan_bytes(queue[0], compact=True)) if compact_fallback else need
             if smallest > mem_budget:
