@@ -92,6 +92,7 @@ struct GatherArgs {
     int ent_bytes;   // 64 * maxe * 8
     int stage_floats;
     int l0, nv;      // views [l0, l0 + nv) of the plan; slab view v holds view l0 + v
+    int nkc;         // runs of kc depth rows per patch
 };
 
 // Consumer threads: 64 destinations x 4 float4 groups of k; one more warp
@@ -222,7 +223,11 @@ __global__ void __launch_bounds__(kGT + 32) k_adj_gather(const __grid_constant__
                                                          const AdjEntry* __restrict__ pent, float* out,
                                                          int accumulate, EmArgs em, int* err)
 {
-    adj_gather_body<MAXE>(&tmap, a, boxes, pent, out, accumulate, em, err, blockIdx.x, blockIdx.y);
+    // the k runs of a patch are adjacent blocks, so they run side by side and the
+    // patch's entries, which each of them reads, come from DRAM about once
+    // (0.246 -> 0.213 ms per 128-view launch against the patch-major order)
+    const int patch = (int)blockIdx.x / a.nkc, kcb = (int)blockIdx.x - patch * a.nkc;
+    adj_gather_body<MAXE>(&tmap, a, boxes, pent, out, accumulate, em, err, patch, kcb);
 }
 
 
@@ -258,7 +263,7 @@ __global__ void __launch_bounds__(kGT + 32) k_adj_gather_grp(const __grid_consta
 {
     const int4 w = group_item(gg.grid);
     const GroupGather& q = gg.p[w.x];
-    adj_gather_body<MAXE>(&q.tmap, q.a, q.boxes, q.pent, q.out, q.accumulate, q.em, q.err, w.y, w.z);
+    adj_gather_body<MAXE>(&q.tmap, q.a, q.boxes, q.pent, q.out, q.accumulate, q.em, q.err, w.z, w.y);
 }
 
 }  // namespace
@@ -369,6 +374,7 @@ cudaError_t gather_setup(const spect_plan_s& P, int l0, int nv, CUtensorMap* map
     a->stage_floats = stage_floats(a->box_floats, a->ent_bytes);
     a->l0 = l0;
     a->nv = nv;
+    a->nkc = (g.nz + kc - 1) / kc;
     return cudaSuccess;
 }
 }  // namespace
@@ -376,14 +382,12 @@ cudaError_t gather_setup(const spect_plan_s& P, int l0, int nv, CUtensorMap* map
 cudaError_t launch_adj_gather(const spect_plan_s& P, int l0, int nv, float* out, int accumulate, EmArgs em,
                               cudaStream_t st)
 {
-    const Geometry& g = P.g;
-    const int kc = gather_kc();
     CUtensorMap map;
     GatherArgs a;
     cudaError_t es = gather_setup(P, l0, nv, &map, &a);
     if (es != cudaSuccess) return es;
     const size_t smem = gather_smem(a.box_floats, a.ent_bytes);
-    const dim3 grid(P.gnpx * P.gnpy, (g.nz + kc - 1) / kc);
+    const dim3 grid(P.gnpx * P.gnpy * a.nkc);  // (patch, k run), the k runs of a patch adjacent
     switch (P.adj_max) {
 #define SPECT_G(M)                                                                                           \
     case M: {                                                                                                \
@@ -434,11 +438,11 @@ cudaError_t build_grouped_gather(const std::vector<spect_plan_s*>& plans, Groupe
                 q.accumulate = 0;
                 q.err = P.err;
                 smem = std::max(smem, gather_smem(q.a.box_floats, q.a.ent_bytes));
-                // the gather's grid: (patch, run of kc depth rows)
-                const int mm = (int)(m - c0), nkc = (P.g.nz + q.a.kc - 1) / q.a.kc;
+                // the gather's grid: (run of kc depth rows, patch), the k runs of a patch adjacent
+                const int mm = (int)(m - c0), nkc = q.a.nkc;
                 if (mm == 0) gg.grid.first[0] = 0;
-                gg.grid.gx[mm] = P.gnpx * P.gnpy;
-                gg.grid.gy[mm] = nkc;
+                gg.grid.gx[mm] = nkc;
+                gg.grid.gy[mm] = P.gnpx * P.gnpy;
                 gg.grid.first[mm + 1] = gg.grid.first[mm] + P.gnpx * P.gnpy * nkc;
                 gg.grid.n = mm + 1;
             }
