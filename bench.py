@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--cpu-views", type=int, default=0, help="views in the CPU baseline sample (0: auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default launch shapes")
+    ap.add_argument("--launch-shape", default=None, metavar="J,ADJ_J,TILES",
+                    help="fix the main plan's launch shape instead of autotuning it (for profiler runs, where the "
+                         "autotuner's timings are distorted)")
     ap.add_argument("--serve-requests", type=int, default=160,
                     help="requests of the serving stream (20 req/s) timed served vs one at a time (0: skip)")
     ap.add_argument("--train-steps", type=int, default=3,
@@ -133,7 +136,7 @@ class Clocks:
 
 # ---------------------------------------------------------------- workload
 def make_workload(device, path, nview=NVIEW, autotune=True, rotation="bilinear", low_memory=False,
-                  recompute=False):
+                  recompute=False, shape=None):
     import torch
 
     from paper_2301_09710_gb300 import SpectPlan, synthetic
@@ -143,7 +146,9 @@ def make_workload(device, path, nview=NVIEW, autotune=True, rotation="bilinear",
     if sep:
         plan = SpectPlan(NX, NZ, nview, mu=prob.mu, dy=prob.dy, fx=prob.fx, fz=prob.fz, device=device,
                          rotation=rotation, low_memory=low_memory, recompute_attenuation=recompute)
-        if autotune and not low_memory:
+        if shape and not low_memory:
+            plan.set_tuning(*shape)
+        elif autotune and not low_memory:
             plan.autotune()  # the library's launch-shape autotuner (timed on this device, outside the timed region)
     else:
         plan = SpectPlan(NX, NZ, nview, mu=prob.mu, dy=prob.dy, psf=prob.full_psf(), device=device,
@@ -219,8 +224,9 @@ def run_ours(args):
     from __graft_entry__ import build
     build()
 
+    shape = tuple(int(v) for v in args.launch_shape.split(",")) if args.launch_shape else None
     prob, plan, x0_h, y_h, rbar_h = make_workload(device, args.path, args.nview, autotune=not args.no_autotune,
-                                                  rotation=args.rotation)
+                                                  rotation=args.rotation, shape=shape)
     info = plan.info()
     launch_shape = plan.tuning if info["fused"] else None
     sep = info["separable"]
