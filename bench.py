@@ -183,7 +183,7 @@ def algorithmic_flops(kind: str, nv: float, sep: bool, fused: bool = False) -> f
 # DRAM bytes (read + write) per 128-view launch of the fused separable kernels, from one ncu capture of the
 # same kernels on the 32-view case of this workload, scaled by 4 (traffic grows with the views); valid for the
 # kernels as captured.
-NCU_TRAFFIC_BYTES_128 = {"conv_adj": 1159.0e6, "conv_fwd": 891.9e6, "rotate_atten": 1404.2e6, "rotate_adj": 775.2e6}
+NCU_TRAFFIC_BYTES_128 = {"conv_adj": 1159.3e6, "conv_fwd": 891.9e6, "rotate_atten": 1404.2e6, "rotate_adj": 775.2e6}
 
 
 def aggregate_timing(total_ms: float, steps: int, world: int, dist=None, device="cpu"):

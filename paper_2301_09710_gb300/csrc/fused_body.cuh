@@ -605,25 +605,33 @@ __device__ __forceinline__ void adj_sep_body(const Geometry& g, const FusedDims&
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         tma_load_1d(MB, mub + (size_t)j_begin * d.ps, SPECT_MBYTES, bar);
     }
-    // edge-class taps of every plane of the group
+    // the detector plane v(:,:,l), transposed, by asynchronous copies issued
+    // next, so their latency overlaps the tap staging and the zeroing below
+    for (int e = tid; e < nz * nvr; e += T) {
+        const int k = e / nvr, r = e - k * nvr;
+        cp_async_4(V + r * d.kpu + ZH + k, vin + (size_t)l * pln + (size_t)k * nx + vlo + r);
+    }
+    // edge-class taps of every plane of the group (zero-padded to P), also asynchronously
     for (int e = tid; e < (j_end - j_begin) * 3 * PT; e += T) {
         const int jj = e / (3 * PT), r3 = e - jj * 3 * PT, c = r3 / PT, a = r3 - c * PT, j = j_begin + jj;
         const int ax = a - ox, az = a - oz;
+        const bool okx = ax >= 0 && ax < g.px, okz = c < cls_z && az >= 0 && az < g.pz;
         float* F = TAP + jj * 6 * PT;
-        F[r3] = (ax >= 0 && ax < g.px) ? __ldg(fx_adj + ((size_t)c * nrow + (size_t)lp * ny + j) * g.px + ax) : 0.f;
-        F[3 * PT + r3] = (c < cls_z && az >= 0 && az < g.pz)
-                             ? __ldg(fz_adj + ((size_t)c * nrow + (size_t)lp * ny + j) * g.pz + az)
-                             : 0.f;
+        cp_async_4_or_zero(F + r3, okx ? fx_adj + ((size_t)c * nrow + (size_t)lp * ny + j) * g.px + ax : fx_adj, okx);
+        cp_async_4_or_zero(F + 3 * PT + r3, okz ? fz_adj + ((size_t)c * nrow + (size_t)lp * ny + j) * g.pz + az : fz_adj,
+                           okz);
     }
 
-    // stage the detector plane v(:,:,l) transposed, zero outside the detector
-    for (int e = tid; e < d.vrows * d.kpu; e += T) V[e] = 0.f;
-    for (int e = tid; e < d.zarea; e += T) Zb[e] = 0.f;
-    __syncthreads();
-    for (int e = tid; e < nz * nvr; e += T) {
-        const int k = e / nvr, r = e - k * nvr;
-        V[r * d.kpu + ZH + k] = vin[(size_t)l * pln + (size_t)k * nx + vlo + r];
+    // zero V outside the detector (the halo columns of the staged rows, and
+    // whole rows beyond them) and Zb; then wait for the staged plane and taps
+    const int halo = d.kpu - nz;  // zero columns of a staged row: [0, ZH) and [ZH + nz, kpu)
+    for (int e = tid; e < nvr * halo; e += T) {
+        const int r = e / halo, c = e - r * halo;
+        V[r * d.kpu + (c < ZH ? c : c + nz)] = 0.f;
     }
+    for (int e = nvr * d.kpu + tid; e < d.vrows * d.kpu; e += T) V[e] = 0.f;
+    for (int e = tid; e < d.zarea; e += T) Zb[e] = 0.f;
+    cp_async_wait_all();
     __syncthreads();
 
     // the thread's first work item of each pass and the step to its next one

@@ -357,6 +357,23 @@ __device__ __forceinline__ void tma_store_wait_read()
 
 __device__ __forceinline__ void tma_store_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+// One 4-byte asynchronous copy global -> shared (cp.async, through L1), and the
+// wait for all of the calling thread's copies.
+__device__ __forceinline__ void cp_async_4(float* dst_smem, const float* src_gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst_smem)), "l"(src_gmem) : "memory");
+}
+
+// The same, writing 0.0f instead of reading when !valid (src is not read then).
+__device__ __forceinline__ void cp_async_4_or_zero(float* dst_smem, const float* src_gmem, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst_smem)), "l"(src_gmem),
+                 "r"(valid ? 4 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Row pitch (floats) of the shared-memory plane images: at least n, a multiple of
 // 4 with pitch/4 odd, so rows are 16-byte aligned and float4 loads with lanes
 // over rows are bank-conflict free.
