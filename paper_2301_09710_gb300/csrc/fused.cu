@@ -744,7 +744,8 @@ int tiles_that_fit(const Geometry& g, size_t limit, int min_tiles)
 }
 
 template <int P>
-cudaError_t fwd_launch(const spect_plan_s& Pl, const float* xt, int l0, int nv, cudaStream_t st)
+cudaError_t fwd_launch(const spect_plan_s& Pl, const float* /*xt: the blur reads the work slab*/, int l0, int nv,
+                       cudaStream_t st)
 {
     const FusedDims d = dims_for<P>(Pl.g, Pl.fused_J, Pl.fused_nT);
     const size_t smem = smem_fwd<P>(Pl.g, d);

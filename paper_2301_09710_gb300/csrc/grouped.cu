@@ -180,7 +180,7 @@ GroupLaunch make_launch(K kern, const A& args, dim3 threads, size_t smem)
 // the launches of one stage for the plans `idx` of bucket P
 template <int P>
 cudaError_t stage_launches(int stage, const std::vector<int>& idx, const std::vector<spect_plan_s*>& plans,
-                           const float* const* y, const float* const* rbar, GroupedBatch& B,
+                           const float* const* y, const float* const* rbar, GroupedBatch& /*B*/,
                            std::vector<GroupLaunch>& out)
 {
     // sub-groups by kernel variant: attenuation staged (rotation) / tiled (blurs)
@@ -249,7 +249,7 @@ cudaError_t stage_by_bucket(int stage, const std::vector<spect_plan_s*>& plans, 
 
 // the depth-group reduce with the EM ratio, all plans (any bucket)
 cudaError_t reduce_launches(const std::vector<spect_plan_s*>& plans, const float* const* y, const float* const* rbar,
-                            GroupedBatch& B, std::vector<GroupLaunch>& out)
+                            GroupedBatch& /*B*/, std::vector<GroupLaunch>& out)
 {
     std::vector<int> all(plans.size());
     std::iota(all.begin(), all.end(), 0);
@@ -274,7 +274,7 @@ cudaError_t reduce_launches(const std::vector<spect_plan_s*>& plans, const float
 
 // x (image layout) <-> x_t ([j][i][k]) for every plan: to_internal / from_internal
 cudaError_t transpose_launches(const std::vector<spect_plan_s*>& plans, float* const* x, bool to_internal,
-                               GroupedBatch& B, std::vector<GroupLaunch>& out)
+                               GroupedBatch& /*B*/, std::vector<GroupLaunch>& out)
 {
     std::vector<int> all(plans.size());
     std::iota(all.begin(), all.end(), 0);

@@ -1152,7 +1152,7 @@ spect_status spect_plan_autotune(spect_plan P, spect_stream stream)
         if (r != SPECT_OK) break;
         if (fJ && aJ && fbest + abest < best_ms) {
             best_ms = fbest + abest;
-            best = {fJ, aJ, t};
+            best = {fJ, aJ, t, 0};
         }
     }
     if (r == SPECT_OK) r = reconfigure(P, best.J, best.adj_J, best.tiles, st);
