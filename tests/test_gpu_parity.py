@@ -231,7 +231,8 @@ def test_column_tiled_fused_kernels(case, monkeypatch):
 
 
 # ---------------------------------------------------------------- patch-staged adjoint gather
-GATHER = [(48, 20, 7, 9, 21), (33, 12, 9, 5, 22), (64, 16, 24, 37, 23), (17, 4, 5, 3, 24), (40, 8, 13, 11, 25)]
+GATHER = [(48, 20, 7, 9, 21), (33, 12, 9, 5, 22), (64, 16, 24, 37, 23), (17, 4, 5, 3, 24), (40, 8, 13, 11, 25),
+          (56, 52, 6, 7, 26)]  # the last: four runs of k per patch (16, 16, 16, 4), a 7 x 7 patch grid
 
 
 @pytest.mark.parametrize("case", GATHER, ids=[f"{c[0]}x{c[1]}v{c[2]}p{c[3]}" for c in GATHER])
